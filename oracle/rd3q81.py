@@ -1,0 +1,412 @@
+"""FP64 CPU oracle for one RD3Q81 lattice Boltzmann step.
+
+Paper: M. Atif, N. H. Maruthi, P. K. Kolluru, C. Thantanapally, S. Ansumali,
+"Lattice Boltzmann Model for Transonic Flows" (arXiv 2409.05114).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference leg of ``bench.py`` may import this module.  The product path (the CUDA library
+and its Python binding) never imports it, and the two share no code, constant table or
+helper: this file rebuilds the velocity set from the paper's table on its own.
+
+Everything is plain numpy float64, in the paper's order and notation, so that it can be
+read against the paper line by line:
+
+* ``velocity_set``        Sec. III + Table "tab:weights": the ten RD3Q81 shells, their
+                          weights as quintic polynomials of theta0, w_0 = 1 - sum(others).
+* ``moments``             Sec. II, Eq. (conslaws): rho, rho*u, rho*u^2 + 3*rho*theta.
+* ``temperature_weights`` App. B, Eq. (zeroveleqseries): the eta^4 series W~_i(theta).
+* ``equilibrium``         App. B, "Discrete equilibrium at nonzero velocity": f~eq with
+                          f^(2), f^(3), R-bar and the tensor R-bar_{kappa alpha zeta eta},
+                          the last two as explicit 81-term sums over W~/rho.
+* ``stream``              Sec. II, Eq. (discretelbm), left side: f_i moves by c_i in one
+                          step.  Half-integer links join the primary lattice (P, integer
+                          positions) and the replica lattice (R, positions + (1/2,1/2,1/2)),
+                          Sec. I (replica grid) and Sec. V (body-centred cubic lattice).
+* ``collide``             Sec. II, Eq. (discretelbm), right side: alpha = 2,
+                          beta = dt / (2 tau + dt) with dt = 1.
+* ``fill_ghosts_x``       Boundary layers in x.  The paper names its own boundary
+                          conditions without formulas; this oracle implements the three the
+                          library offers (periodic, zero-gradient outflow, equilibrium
+                          inflow), each defined in its docstring.
+
+Parity pins (tests/test_oracle_*.py): lattice identities in exact arithmetic, the paper's
+printed moment-error column, W~ against its closed-form generating function, equilibrium
+moments, uniform-state fixed points, conservation on periodic grids, cubic-symmetry
+equivariance, the closed-form sound speed and the exact Sod/Riemann solution.  No function
+here is "parity unpinned".
+
+Array conventions (all float64):
+    populations  f[s, i, z, y, x]   s = 0 (P) or 1 (R), i = direction (this module's order)
+    fields       rho[s, z, y, x], theta[s, z, y, x], u[a, s, z, y, x] with a = x, y, z
+"""
+
+from __future__ import annotations
+
+from fractions import Fraction
+from itertools import permutations, product
+
+import numpy as np
+
+# theta0 as printed under Table "tab:weights" (Sec. III).
+THETA0_TEXT = "0.821035006329447750282591763"
+THETA0 = float(THETA0_TEXT)
+
+# Table "tab:weights": shell name, one generating velocity in half units h = 2c, and the
+# weight as {power of theta0: integer coefficient} over an integer denominator.
+_SHELLS = (
+    ("SC-1", (2, 0, 0), {1: 388800, 2: -2508408, 3: 7033852, 4: -7856469, 5: 2838528}, 486000),
+    ("SC-2", (4, 0, 0), {1: -388800, 2: 3091608, 3: -8269102, 4: 8694819, 5: -2838528}, 3888000),
+    ("SC-3", (6, 0, 0), {1: 388800, 2: -3199608, 3: 8977852, 4: -9120069, 5: 2838528}, 30618000),
+    ("SC-4", (8, 0, 0), {1: -97200, 2: 809352, 3: -2315338, 4: 2396961, 5: -709632}, 108864000),
+    ("FCC-1", (2, 2, 0), {3: 8, 4: -9}, 12),
+    ("FCC-2", (4, 4, 0), {3: -2, 4: 9}, 768),
+    ("BCC-1/2", (1, 1, 1), {2: 24300, 3: -103834, 4: 126963, 5: -44352}, 7776),
+    ("BCC-1", (2, 2, 2), {2: -24300, 3: 189022, 4: -328275, 5: 177408}, 272160),
+    ("BCC-3/2", (3, 3, 3), {2: 2700, 3: -24778, 4: 67995, 5: -44352}, 699840),
+    ("BCC-5/2", (5, 5, 5), {2: -972, 3: 11818, 4: -43371, 5: 44352}, 68040000),
+)
+
+
+def shell_weight_exact(coeffs: dict, den: int, theta0: Fraction) -> Fraction:
+    """One row of Table "tab:weights": sum_k coeffs[k] * theta0**k / den, exactly."""
+    return sum((Fraction(c) * theta0 ** k for k, c in coeffs.items()), Fraction(0)) / den
+
+
+def _shell_vectors(gen):
+    """All distinct vectors obtained from ``gen`` by permuting and sign-flipping components
+    (the SC, FCC and BCC shells of App. A)."""
+    out = set()
+    for perm in permutations(gen):
+        for signs in product((1, -1), repeat=3):
+            out.add(tuple(s * p for s, p in zip(signs, perm)))
+    return sorted(out)
+
+
+class Lattice:
+    """The RD3Q81 velocity set (Sec. III, Table "tab:weights").
+
+    Attributes
+    ----------
+    h      : int64[81, 3]  velocities in half units, h = 2 c
+    c      : float64[81, 3] velocities c_i (components in {0, +-1/2, +-1, ..., +-4})
+    c2     : float64[81]   |c_i|^2
+    w      : float64[81]   weights w_i = W_i(theta0); w_0 = 1 - sum of the others
+    shell  : list[str]     shell name of each direction ("rest" for i = 0)
+    theta0 : float         reference temperature
+    """
+
+    def __init__(self, theta0_text: str = THETA0_TEXT):
+        t0 = Fraction(theta0_text)
+        hs, ws, names = [(0, 0, 0)], [None], ["rest"]
+        for name, gen, coeffs, den in _SHELLS:
+            wt = shell_weight_exact(coeffs, den, t0)
+            for v in _shell_vectors(gen):
+                hs.append(v)
+                ws.append(wt)
+                names.append(name)
+        ws[0] = Fraction(1) - sum(ws[1:], Fraction(0))
+        self.h = np.array(hs, dtype=np.int64)
+        self.c = self.h.astype(np.float64) / 2.0
+        self.c2 = (self.c ** 2).sum(axis=1)
+        self.w = np.array([float(x) for x in ws])
+        self.w_exact = ws
+        self.shell = names
+        self.theta0 = float(t0)
+        self.q = len(hs)
+
+
+_LAT = None
+
+
+def velocity_set() -> Lattice:
+    """The (cached) RD3Q81 lattice."""
+    global _LAT
+    if _LAT is None:
+        _LAT = Lattice()
+    return _LAT
+
+
+# ---------------------------------------------------------------------------------------
+# Moments, Sec. II Eq. (conslaws)
+# ---------------------------------------------------------------------------------------
+
+def moments(f: np.ndarray, lat: Lattice | None = None):
+    """rho = <f, 1>, rho u_a = <f, c_a>, rho u^2 + 3 rho theta = <f, c^2>.
+
+    ``f`` has the direction index first: f[i, ...].  Returns (rho, u[3, ...], theta).
+    """
+    lat = lat or velocity_set()
+    rho = np.tensordot(np.ones(lat.q), f, axes=(0, 0))
+    j = np.tensordot(lat.c.T, f, axes=(1, 0))
+    e = np.tensordot(lat.c2, f, axes=(0, 0))
+    u = j / rho
+    theta = (e - rho * (u ** 2).sum(axis=0)) / (3.0 * rho)
+    return rho, u, theta
+
+
+# ---------------------------------------------------------------------------------------
+# Equilibrium, App. B
+# ---------------------------------------------------------------------------------------
+
+def temperature_weights(rho: np.ndarray, theta: np.ndarray, lat: Lattice | None = None):
+    """W~_i(theta), App. B Eq. (zeroveleqseries), kept to eta^4 as printed there.
+
+    W~_i = rho w_i [1 + eta/2 (y-3) + eta^2/8 (y^2 - 10y + 15)
+                    + eta^3/48 (y^3 - 21y^2 + 105y - 105)
+                    + eta^4/384 (y^4 - 36y^3 + 378y^2 - 1260y + 945)],
+    with y_i = c_i^2 / theta0 and eta = theta/theta0 - 1.   Returns W[i, ...].
+    """
+    lat = lat or velocity_set()
+    t0 = lat.theta0
+    eta = theta / t0 - 1.0
+    shape = (lat.q,) + (1,) * np.ndim(theta)
+    y = (lat.c2 / t0).reshape(shape)
+    w = lat.w.reshape(shape)
+    # the bracket's coefficient of eta^k, per direction
+    p1 = (y - 3.0) / 2.0
+    p2 = (y ** 2 - 10.0 * y + 15.0) / 8.0
+    p3 = (y ** 3 - 21.0 * y ** 2 + 105.0 * y - 105.0) / 48.0
+    p4 = (y ** 4 - 36.0 * y ** 3 + 378.0 * y ** 2 - 1260.0 * y + 945.0) / 384.0
+    poly = 1.0 + eta * p1 + eta ** 2 * p2 + eta ** 3 * p3 + eta ** 4 * p4
+    return rho * w * poly
+
+
+def rbar(theta: np.ndarray, lat: Lattice | None = None, Wn: np.ndarray | None = None) -> np.ndarray:
+    """Rb = <W~/rho, c^4> / (15 theta^2) - 1 (App. B), as an explicit 81-term sum.
+    ``Wn`` may pass W~/rho at these temperatures if the caller already has it."""
+    lat = lat or velocity_set()
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    if Wn is None:
+        Wn = temperature_weights(np.ones_like(th), th, lat)
+    return (lat.c2 ** 2) @ Wn / (15.0 * th ** 2) - 1.0
+
+
+def rbar_tensor_contraction(theta: np.ndarray, u: np.ndarray, lat: Lattice | None = None,
+                            Wn: np.ndarray | None = None):
+    """u_a u_z u_e c_ix Rb_{x a z e} for every direction i (App. B), with
+    Rb_{k a z e} = <W~/rho, c_k c_a c_z c_e> / theta^2 - Delta_{a k e z} written out as
+    sum_j (W~_j/rho)(c_j.c_i)(c_j.u)^3 / theta^2 - 3 u^2 (u.c_i).   Returns [81, n].
+    ``Wn`` may pass W~/rho at these temperatures if the caller already has it."""
+    lat = lat or velocity_set()
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    u1 = np.asarray(u, dtype=np.float64).reshape(3, -1)
+    if Wn is None:
+        Wn = temperature_weights(np.ones_like(th), th, lat)
+    xi = lat.c @ u1
+    q = (u1 ** 2).sum(axis=0)
+    G = lat.c @ lat.c.T                                   # c_i . c_j   [81, 81]
+    return G @ (Wn * xi * xi * xi) / th ** 2 - 3.0 * q * xi
+
+
+def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None = None):
+    """Series entropic equilibrium f~eq_i(rho, u, theta) of App. B (nonzero velocity):
+
+        f~eq_i = W~_i(theta) [1 + u.c_i/theta + f_i^(2) + f_i^(3)]
+
+        f^(2) = u_a u_b (c_a c_b - theta delta_ab) / (2 theta^2)
+                - (5/3) u^2/(2 theta^2) * Rb/(2 + 5 Rb) * (c^2 - 3 theta)
+        f^(3) = u_a u_b u_g (c_a c_b c_g - theta c_k Delta_abgk) / (6 theta^3)
+                - [5/(6 theta^3) * Rb u^2/(2 + 5 Rb)] (u.c) (c^2 - 3 theta)
+                + (5 (u.c) u^2 Rb - u_a u_z u_e c_x Rb_{x a z e}) / (6 theta^2)
+
+    with  Rb_{k a z e} = <W~/rho, c_k c_a c_z c_e> / theta^2 - Delta_{a k e z}
+    and   Rb           = <W~/rho, c^4> / (15 theta^2) - 1.
+
+    W~ in the two Rb definitions is taken per unit density (W~/rho), which is the reading
+    that makes both vanish at theta = theta0.  The contractions are written out:
+        u_a u_b u_g c_k Delta_abgk         = 3 u^2 (u.c)
+        u_a u_z u_e c_ix Rb_{x a z e}      = sum_j (W~_j/rho) (c_j.c_i) (c_j.u)^3 / theta^2
+                                             - 3 u^2 (u.c_i)
+    Inputs are arrays over sites (any shape S, u is [3, *S]); returns feq[81, *S].
+    """
+    lat = lat or velocity_set()
+    rho = np.asarray(rho, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    S = rho.shape
+    rho1, th = rho.reshape(-1), theta.reshape(-1)
+    u1 = u.reshape(3, -1)
+
+    W = temperature_weights(rho1, th, lat)               # [81, n]
+    q = (u1 ** 2).sum(axis=0)                             # u^2
+    xi = lat.c @ u1                                       # u.c_i      [81, n]
+    c2 = lat.c2[:, None]
+    Wn = W / rho1                                         # W~ / rho
+    Rb = rbar(th, lat, Wn)
+    Rcontr = rbar_tensor_contraction(th, u1, lat, Wn)
+
+    K = Rb / (2.0 + 5.0 * Rb)
+    f1 = xi / th
+    f2 = ((xi ** 2 - th * q) / (2.0 * th ** 2)
+          - (5.0 / 3.0) * q / (2.0 * th ** 2) * K * (c2 - 3.0 * th))
+    f3 = ((xi * xi * xi - th * 3.0 * q * xi) / (6.0 * th ** 3)
+          - (5.0 / (6.0 * th ** 3) * K * q) * xi * (c2 - 3.0 * th)
+          + (5.0 * xi * q * Rb - Rcontr) / (6.0 * th ** 2))
+    feq = W * (1.0 + f1 + f2 + f3)
+    return feq.reshape((lat.q,) + S)
+
+
+# ---------------------------------------------------------------------------------------
+# Streaming on the primary + replica (BCC) lattice, Sec. II Eq. (discretelbm)
+# ---------------------------------------------------------------------------------------
+
+def pull_displacement(h: np.ndarray, target_sub: int):
+    """Index displacement d (out[n] = src[n - d]) and source sublattice for pulling the
+    population with half-unit velocity h into a site of sublattice ``target_sub``.
+
+    A P site with index n sits at n, an R site with index n at n + (1/2, 1/2, 1/2).  The
+    population arriving at position p left p - c = p - h/2 one step earlier:
+      * h even (integer link): same sublattice, d = h/2;
+      * h odd, target P:  source position n - h/2 is the R site with index n - (h+1)/2;
+      * h odd, target R:  source position n + 1/2 - h/2 is the P site n - (h-1)/2.
+    """
+    h = np.asarray(h)
+    if np.all(h % 2 == 0):
+        return h // 2, target_sub
+    if target_sub == 0:
+        return (h + 1) // 2, 1
+    return (h - 1) // 2, 0
+
+
+def fill_ghosts_x(fs: np.ndarray, bc_lo, bc_hi, feq_lo=None, feq_hi=None, width: int = 4):
+    """Extend one sublattice's populations fs[i, z, y, x] by ``width`` ghost layers at each
+    x face.  Returns ext[i, z, y, x + width].
+
+    Boundary kinds (one per face):
+      "periodic"      ghosts are the interior layers of the opposite side (wrap-around);
+      "zero_gradient" every ghost layer copies all populations of the nearest interior
+                      layer of the same sublattice (same y, z) -- an outflow face;
+      "eq_inflow"     every ghost site holds feq(rho_in, u_in, theta_in) (``feq_lo`` /
+                      ``feq_hi``: the 81 values, identical on both sublattices).
+    """
+    q, nz, ny, nx = fs.shape
+    ext = np.empty((q, nz, ny, nx + 2 * width))
+    ext[..., width:width + nx] = fs
+    for side, kind, feq in (("lo", bc_lo, feq_lo), ("hi", bc_hi, feq_hi)):
+        sl = slice(0, width) if side == "lo" else slice(width + nx, 2 * width + nx)
+        if kind == "periodic":
+            src = fs[..., nx - width:] if side == "lo" else fs[..., :width]
+            if nx < width:  # wrap more than once
+                idx = (np.arange(-width, 0) if side == "lo" else np.arange(nx, nx + width)) % nx
+                src = fs[..., idx]
+            ext[..., sl] = src
+        elif kind == "zero_gradient":
+            edge = fs[..., 0:1] if side == "lo" else fs[..., nx - 1:nx]
+            ext[..., sl] = edge
+        elif kind == "eq_inflow":
+            ext[..., sl] = np.asarray(feq, dtype=np.float64).reshape(q, 1, 1, 1)
+        else:
+            raise ValueError(f"unknown boundary kind {kind!r}")
+    return ext
+
+
+def stream(f: np.ndarray, bc=("periodic", "periodic"), feq_in=(None, None),
+           lat: Lattice | None = None):
+    """Pull streaming: f_pre[s, i, n] = f_post[src_sub, i, n - d] for every site of both
+    sublattices (left-hand side of Eq. (discretelbm) with dt = 1).
+
+    y and z are periodic; ``bc`` gives the kinds of the -x and +x faces (see
+    ``fill_ghosts_x``); ``feq_in`` the inflow populations of those faces (or None).
+    """
+    lat = lat or velocity_set()
+    width = 4
+    ext = [fill_ghosts_x(f[s], bc[0], bc[1], feq_in[0], feq_in[1], width) for s in (0, 1)]
+    nx = f.shape[-1]
+    out = np.empty_like(f)
+    for s in (0, 1):
+        for i in range(lat.q):
+            d, src = pull_displacement(lat.h[i], s)
+            dx, dy, dz = (int(v) for v in d)
+            a = ext[src][i]                               # [z, y, x + width]
+            a = a[:, :, width - dx:width - dx + nx]        # out[x] = ext[x + width - dx]
+            a = np.roll(a, shift=(dz, dy), axis=(0, 1))    # out[n] = src[n - d] in y, z
+            out[s, i] = a
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Collision, Sec. II Eq. (discretelbm)
+# ---------------------------------------------------------------------------------------
+
+def beta_of_tau(tau: float) -> float:
+    """beta = dt / (2 tau + dt) with dt = 1 (Sec. II, below Eq. (discretelbm))."""
+    return 1.0 / (2.0 * tau + 1.0)
+
+
+def collide(f: np.ndarray, feq: np.ndarray, tau: float) -> np.ndarray:
+    """f + alpha beta (feq - f) with alpha = 2 (Eq. (discretelbm))."""
+    return f + 2.0 * beta_of_tau(tau) * (feq - f)
+
+
+# ---------------------------------------------------------------------------------------
+# Whole steps
+# ---------------------------------------------------------------------------------------
+
+def init(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None = None,
+         chunk: int = 1024):
+    """Populations f[s, i, z, y, x] = feq(rho, u, theta) at every site of both sublattices.
+
+    rho, theta: [2, nz, ny, nx]; u: [3, 2, nz, ny, nx]."""
+    lat = lat or velocity_set()
+    rho = np.asarray(rho, dtype=np.float64)
+    S = rho.shape
+    r1 = rho.reshape(-1)
+    t1 = np.asarray(theta, dtype=np.float64).reshape(-1)
+    u1 = np.asarray(u, dtype=np.float64).reshape(3, -1)
+    out = np.empty((lat.q, r1.size))
+    for a in range(0, r1.size, chunk):
+        b = min(a + chunk, r1.size)
+        out[:, a:b] = equilibrium(r1[a:b], u1[:, a:b], t1[a:b], lat)
+    return np.moveaxis(out.reshape((lat.q,) + S), 0, 1).copy()
+
+
+def bc_feq(bc_spec, lat: Lattice | None = None):
+    """81 inflow populations of an "eq_inflow" face spec ("eq_inflow", rho, ux, uy, uz, theta),
+    else None."""
+    if bc_spec[0] != "eq_inflow":
+        return None
+    _, r, ux, uy, uz, t = bc_spec
+    return equilibrium(np.array([r]), np.array([[ux], [uy], [uz]]), np.array([t]), lat)[:, 0]
+
+
+def step(f: np.ndarray, tau: float, bc_x=(("periodic",), ("periodic",)),
+         lat: Lattice | None = None, chunk: int = 1024) -> np.ndarray:
+    """One time step: boundary fill, pull streaming, moments, equilibrium, BGK collision.
+
+    ``bc_x`` holds the -x and +x face specs: ("periodic",), ("zero_gradient",) or
+    ("eq_inflow", rho, ux, uy, uz, theta)."""
+    lat = lat or velocity_set()
+    kinds = (bc_x[0][0], bc_x[1][0])
+    if (kinds[0] == "periodic") != (kinds[1] == "periodic"):
+        raise ValueError("a periodic x face must be paired with a periodic x face")
+    feq_in = (bc_feq(bc_x[0], lat), bc_feq(bc_x[1], lat))
+    pre = stream(f, kinds, feq_in, lat)
+    flat = np.moveaxis(pre, 1, 0).reshape(lat.q, -1)     # [81, sites]
+    post = np.empty_like(flat)
+    for a in range(0, flat.shape[1], chunk):
+        b = min(a + chunk, flat.shape[1])
+        rho, u, theta = moments(flat[:, a:b], lat)
+        feq = equilibrium(rho, u, theta, lat)
+        post[:, a:b] = collide(flat[:, a:b], feq, tau)
+    return np.moveaxis(post.reshape((lat.q,) + f.shape[:1] + f.shape[2:]), 0, 1).copy()
+
+
+def run(f: np.ndarray, tau: float, nsteps: int, bc_x=(("periodic",), ("periodic",)),
+        lat: Lattice | None = None) -> np.ndarray:
+    for _ in range(nsteps):
+        f = step(f, tau, bc_x, lat)
+    return f
+
+
+def fields(f: np.ndarray, lat: Lattice | None = None):
+    """(rho[2,z,y,x], u[3,2,z,y,x], theta[2,z,y,x]) of stored populations f[s, i, z, y, x]."""
+    lat = lat or velocity_set()
+    return moments(np.moveaxis(f, 1, 0), lat)
+
+
+def totals(f: np.ndarray, lat: Lattice | None = None):
+    """Global sums (sum rho, sum rho u_x, sum rho u_y, sum rho u_z, sum <f, c^2>) over all
+    sites: the conserved quantities of Eq. (conslaws) summed over the grid."""
+    lat = lat or velocity_set()
+    g = np.moveaxis(f, 1, 0).reshape(lat.q, -1).sum(axis=1)
+    return np.array([g.sum(), *(lat.c.T @ g), lat.c2 @ g])

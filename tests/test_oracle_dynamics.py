@@ -1,0 +1,217 @@
+"""Pins of the oracle's streaming, collision and boundary fills (Sec. II, Eq. (discretelbm);
+replica / BCC lattice of Sec. I and Sec. V):
+
+* brute force on tiny grids: every pulled population is the one found by searching the
+  site whose physical position is (target position - c_i), periodic or through the
+  boundary layers (zero gradient, equilibrium inflow);
+* a uniform state is a fixed point (periodic and inflow/outflow), even at Mach 2;
+* sum rho, sum rho u, sum <f, c^2> are conserved to round-off on periodic grids;
+* one step commutes with the cubic symmetries of the P+R lattice;
+* a small-amplitude standing wave oscillates at the closed-form adiabatic sound speed
+  c_s = sqrt(5 theta0 / 3) (Sec. IV C: c_s = sqrt(gamma theta0), gamma = 5/3);
+* the Sod shock tube follows the exact Euler Riemann solution (gamma = 5/3).
+"""
+
+from itertools import permutations, product
+
+import numpy as np
+import pytest
+
+from oracle import rd3q81 as O
+from riemann_exact import sample
+
+LAT = O.velocity_set()
+T0 = LAT.theta0
+CS = np.sqrt(5.0 * T0 / 3.0)
+
+
+def _positions(nx, ny, nz):
+    """Physical positions pos[s, a, z, y, x] of both sublattices."""
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    P = np.stack([x, y, z]).astype(float)
+    return np.stack([P, P + 0.5])
+
+
+def _brute_pull(f, bc_lo, bc_hi, feq_lo=None, feq_hi=None):
+    """Reference pull by physical positions: for every target site and direction, find
+    the source site at (position - c_i); periodic in y, z; in x either periodic or clamped
+    to the nearest interior site of the same sublattice (zero gradient) or replaced by the
+    inflow equilibrium."""
+    _, q, nz, ny, nx = f.shape
+    out = np.empty_like(f)
+    for s in (0, 1):
+        for i in range(q):
+            c = LAT.c[i]
+            for z in range(nz):
+                for y in range(ny):
+                    for x in range(nx):
+                        p = np.array([x, y, z], float) + 0.5 * s - c
+                        src = 0 if float(p[0]).is_integer() else 1
+                        m = np.floor(p).astype(int)
+                        mz, my = m[2] % nz, m[1] % ny
+                        mx = m[0]
+                        if mx < 0 or mx >= nx:
+                            kind, feq = (bc_lo, feq_lo) if mx < 0 else (bc_hi, feq_hi)
+                            if kind == "periodic":
+                                mx %= nx
+                            elif kind == "zero_gradient":
+                                mx = 0 if mx < 0 else nx - 1
+                            else:
+                                out[s, i, z, y, x] = feq[i]
+                                continue
+                        out[s, i, z, y, x] = f[src, i, mz, my, mx]
+    return out
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (9, 1, 2)])
+def test_stream_periodic_brute_force(dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(7)
+    f = rng.random((2, 81, nz, ny, nx))
+    got = O.stream(f)
+    ref = _brute_pull(f, "periodic", "periodic")
+    np.testing.assert_array_equal(got, ref)
+    # a permutation: nothing is lost or duplicated
+    np.testing.assert_array_equal(np.sort(got.ravel()), np.sort(f.ravel()))
+
+
+def test_stream_boundaries_brute_force():
+    nx, ny, nz = 7, 3, 2
+    rng = np.random.default_rng(8)
+    f = rng.random((2, 81, nz, ny, nx))
+    feq_hi = O.bc_feq(("eq_inflow", 0.9, -0.3, 0.1, 0.05, T0 * 1.05))
+    got = O.stream(f, ("zero_gradient", "eq_inflow"), (None, feq_hi))
+    ref = _brute_pull(f, "zero_gradient", "eq_inflow", None, feq_hi)
+    np.testing.assert_array_equal(got, ref)
+    feq_lo = O.bc_feq(("eq_inflow", 1.1, 0.4, 0.0, 0.0, T0))
+    got = O.stream(f, ("eq_inflow", "zero_gradient"), (feq_lo, None))
+    ref = _brute_pull(f, "eq_inflow", "zero_gradient", feq_lo, None)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mach,eta", [(0.0, 0.0), (0.7, 0.2), (2.0, 0.0)])
+def test_uniform_state_is_fixed_point(mach, eta):
+    nx, ny, nz = 6, 4, 3
+    u0 = np.array([mach * CS * 0.8, -mach * CS * 0.6, 0.0])
+    rho = np.full((2, nz, ny, nx), 1.2)
+    th = np.full_like(rho, T0 * (1 + eta))
+    u = np.broadcast_to(u0.reshape(3, 1, 1, 1, 1), (3,) + rho.shape).copy()
+    f0 = O.init(rho, u, th)
+    f = O.run(f0, 0.05, 3)
+    assert np.abs(f - f0).max() <= 1e-12 * np.abs(f0).max()
+    # inflow of the same state at -x, zero-gradient outflow at +x
+    bc = (("eq_inflow", 1.2, *u0, T0 * (1 + eta)), ("zero_gradient",))
+    f = O.run(f0, 0.05, 3, bc)
+    assert np.abs(f - f0).max() <= 1e-12 * np.abs(f0).max()
+
+
+def _smooth_state(nx, ny, nz, amp, seed):
+    rng = np.random.default_rng(seed)
+    pos = _positions(nx, ny, nz)
+    k = 2 * np.pi / np.array([nx, ny, nz], float).reshape(1, 3, 1, 1, 1)
+    ph = rng.random((4, 3)) * 2 * np.pi
+
+    def wave(j, scale):
+        return scale * np.sin(k[0, 0] * pos[:, 0] + ph[j, 0]) * \
+            np.cos(k[0, 1] * pos[:, 1] + ph[j, 1]) * np.cos(k[0, 2] * pos[:, 2] + ph[j, 2])
+
+    rho = 1.0 + amp * wave(0, 0.2)
+    th = T0 * (1.0 + amp * wave(1, 0.1))
+    u = np.stack([amp * CS * wave(2, 1.0), -amp * CS * wave(3, 1.0), 0.5 * amp * CS * wave(0, 1.0)])
+    return rho, u, th
+
+
+def test_conservation_periodic():
+    rho, u, th = _smooth_state(7, 6, 5, 0.5, 3)
+    f = O.init(rho, u, th)
+    t_init = O.totals(f)
+    f = O.run(f, 0.02, 5)
+    t_end = O.totals(f)
+    scale = np.array([t_init[0], t_init[0], t_init[0], t_init[0], t_init[4]])
+    assert np.all(np.abs(t_end - t_init) <= 1e-12 * scale), (t_end - t_init)
+
+
+def _transform(f, M):
+    """Apply the cubic symmetry M (signed permutation matrix) to populations on a cubic
+    periodic P+R grid: position p -> M p, velocity c -> M c."""
+    _, q, n, _, _ = f.shape
+    index = {tuple(h): i for i, h in enumerate(LAT.h)}
+    perm = [index[tuple((M @ h).astype(int))] for h in LAT.h]
+    out = np.empty_like(f)
+    s_vec = M @ np.ones(3)
+    for s in (0, 1):
+        for z, y, x in product(range(n), repeat=3):
+            m = M @ np.array([x, y, z])
+            if s == 1:
+                m = m + (s_vec - 1) / 2
+            mx, my, mz = (int(v) % n for v in m)
+            out[s, perm, mz, my, mx] = f[s, :, z, y, x]
+    return out
+
+
+@pytest.mark.parametrize("mi", [1, 7, 20, 33, 47])
+def test_step_cubic_equivariance(mi):
+    mats = []
+    for perm in permutations(range(3)):
+        for signs in product((1, -1), repeat=3):
+            M = np.zeros((3, 3))
+            for r, (p, sg) in enumerate(zip(perm, signs)):
+                M[r, p] = sg
+            mats.append(M)
+    M = mats[mi]
+    rho, u, th = _smooth_state(5, 5, 5, 0.4, 11)
+    f = O.init(rho, u, th)
+    a = _transform(O.run(f, 0.03, 2), M)
+    b = O.run(_transform(f, M), 0.03, 2)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+
+
+def test_sound_speed():
+    nx = 64
+    k = 2 * np.pi / nx
+    pos = _positions(nx, 1, 1)[:, 0]
+    eps = 1e-4
+    rho = np.ones((2, 1, 1, nx))
+    th = np.full_like(rho, T0)
+    u = np.zeros((3,) + rho.shape)
+    u[0] = eps * np.sin(k * pos)
+    f = O.init(rho, u, th)
+    amp = []
+    nsteps = int(2.2 * nx / CS)
+    basis = np.sin(k * pos)
+    for _ in range(nsteps):
+        f = O.step(f, 0.1)
+        _, uu, _ = O.fields(f)
+        amp.append((uu[0] * basis).sum() / (basis ** 2).sum())
+    from scipy.optimize import curve_fit
+    t = np.arange(1, nsteps + 1)
+    model = lambda t, A, w, g, ph: A * np.cos(w * t + ph) * np.exp(-g * t)
+    p, _ = curve_fit(model, t, np.array(amp), p0=[eps, CS * k, 1e-3, 0.0])
+    assert abs(p[1] / k / CS - 1.0) < 1e-3, p[1] / k
+    assert p[2] > 0.0
+
+
+def test_sod_against_exact_riemann():
+    """Sod tube rho 1 | 0.125, theta theta0 | 0.8 theta0 (p = rho theta), zero-gradient x
+    faces, tau = 0.6 in the paper's convention (beta = 1/(2 tau + 1)), 100 steps, compared
+    with the exact solution for gamma = 5/3 (monatomic: E = rho u^2 + 3 rho theta)."""
+    nx, steps = 512, 100
+    pos = _positions(nx, 1, 1)[:, 0]
+    left = pos < nx / 2
+    rho = np.where(left, 1.0, 0.125)
+    th = np.where(left, T0, 0.8 * T0)
+    u = np.zeros((3,) + rho.shape)
+    f = O.init(rho, u, th)
+    f = O.run(f, 0.6, steps, (("zero_gradient",), ("zero_gradient",)))
+    r, uu, tt = O.fields(f)
+    x = pos.reshape(-1)
+    o = np.argsort(x)
+    x, R, U, P = x[o], r.reshape(-1)[o], uu[0].reshape(-1)[o], (r * tt).reshape(-1)[o]
+    re, ue, pe, info = sample((1.0, 0.0, T0), (0.125, 0.0, 0.1 * T0), 5.0 / 3.0, (x - nx / 2) / steps)
+    x_shock = x[np.where(R > 0.5 * (info["rho_star_right"] + 0.125))[0].max()]
+    assert abs(x_shock - (nx / 2 + info["s_shock"] * steps)) < 2.0
+    plateau = (x > nx / 2 + info["s_tail"] * steps + 8) & (x < nx / 2 + info["s_shock"] * steps - 8)
+    assert abs(U[plateau].mean() / info["u_star"] - 1) < 0.01
+    assert abs(P[plateau].mean() / info["p_star"] - 1) < 0.01
+    assert np.abs(R - re).mean() < 0.015
+    assert np.abs(U - ue).mean() < 0.02
