@@ -1,0 +1,162 @@
+/*
+ * liblbm_rd3q81 -- GB300 (sm_103a) implementation of the RD3Q81 lattice Boltzmann step.
+ *
+ * Paper: M. Atif, N. H. Maruthi, P. K. Kolluru, C. Thantanapally, S. Ansumali,
+ * "Lattice Boltzmann Model for Transonic Flows", arXiv 2409.05114.
+ *
+ * One step (lbm_step) is, for every site x of the grid and every velocity c_i,
+ *   f_i(x + c_i, t + 1) = f_i(x, t) + alpha beta [f~eq_i(rho, u, theta) - f_i(x, t)]
+ * with alpha = 2 and beta = 1 / (2 tau + 1) (Sec. II, Eq. (discretelbm)); rho, rho u and
+ * rho u^2 + 3 rho theta are the moments <f, 1>, <f, c>, <f, c^2> (Eq. (conslaws)); f~eq is
+ * the series entropic equilibrium with temperature-dependent weights W~_i(theta) to eta^4,
+ * f^(2), f^(3) and R-bar (App. B); the 81 velocities and weights are Table "tab:weights".
+ *
+ * Grid.  The physical lattice is body-centred cubic: a primary sublattice P (site index
+ * n = (x, y, z), position n) and a replica sublattice R (same index range, position
+ * n + (1/2, 1/2, 1/2)).  Half-integer velocities (BCC-1/2, 3/2, 5/2) move populations
+ * between P and R (Sec. I, replica grid).  A grid nx*ny*nz therefore has 2*nx*ny*nz sites.
+ *
+ * Field layout (lbm_init, lbm_moments): site-major, all P sites then all R sites, each
+ * block ordered z, y, x with x fastest: site k = sub*nx*ny*nz + (z*ny + y)*nx + x.
+ * Scalars rho[k], theta[k] have 2*nx*ny*nz entries; velocity u is [3][2*nx*ny*nz]
+ * (all u_x, then all u_y, then all u_z).
+ * Population layout (lbm_get_populations / lbm_set_populations): dense FP64
+ * f[sub][i][z][y][x], i in the library's direction order (lbm_velocities).
+ *
+ * Memory.  The context owns its device memory (two population buffers, ping-pong).  The
+ * caller owns every field buffer it passes; the library copies in or out and keeps no
+ * caller pointer after a call returns.  on_device = 1 means the pointers are device
+ * pointers of the context's device (for example a torch tensor's data_ptr()), read or
+ * written in order on the context's stream; on_device = 0 means host memory.
+ *
+ * Errors.  Every call returns an lbm_status; no C++ exception crosses this interface.
+ * A NULL or destroyed context gives LBM_EINVAL.  lbm_last_error() describes the last
+ * failure.  LBM_EUNSTABLE is returned by the synchronising calls once any site has seen a
+ * non-finite value, rho <= 0 or theta <= 0 (the series equilibrium has a limited range in
+ * temperature deviation and Mach number; the populations are left as computed).
+ *
+ * Threads.  Calls on one context must not overlap; different contexts are independent.
+ */
+#ifndef LBM_RD3Q81_H
+#define LBM_RD3Q81_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,    /* invalid argument or configuration */
+  LBM_ENOMEM = 2,    /* device memory (or the server's HBM budget) exhausted */
+  LBM_ECUDA = 3,     /* a CUDA call failed; see lbm_last_error */
+  LBM_EUNSTABLE = 4, /* a site saw rho <= 0, theta <= 0 or a non-finite value */
+  LBM_ETIMEOUT = 5,  /* a bounded wait ran out */
+  LBM_EBUSY = 6,     /* result not ready yet (serving) */
+  LBM_ENOTFOUND = 7  /* unknown ticket (serving) */
+} lbm_status;
+
+typedef enum { LBM_RD3Q81 = 1 } lbm_velset;
+
+typedef enum {
+  LBM_BC_PERIODIC = 0,      /* wrap-around; the opposite face must be periodic too */
+  LBM_BC_ZERO_GRADIENT = 1, /* outflow: ghost sites copy the nearest interior site of the
+                               same sublattice (all 81 populations) before every step */
+  LBM_BC_EQ_INFLOW = 2      /* ghost sites hold f~eq(rho, u, theta) of the face's state */
+} lbm_bc_kind;
+
+typedef enum {
+  LBM_F64 = 0,        /* populations stored as FP64, all arithmetic FP64 */
+  LBM_F32 = 1,        /* stored as FP32, collide in FP32 */
+  LBM_F16_OFFSET = 2, /* stored as FP16 offsets d_i = f_i / w_i - 1, collide in FP32 */
+  LBM_BF16_OFFSET = 3 /* stored as BF16 offsets d_i = f_i / w_i - 1, collide in FP32 */
+} lbm_storage;
+
+typedef struct {
+  int kind;                          /* lbm_bc_kind */
+  double rho, ux, uy, uz, theta;     /* state of an LBM_BC_EQ_INFLOW face; ignored otherwise */
+} lbm_bc;
+
+typedef struct {
+  int nx, ny, nz;     /* sites per sublattice along x, y, z (each >= 1) */
+  int velset;         /* LBM_RD3Q81 */
+  double tau;         /* the paper's relaxation time: beta = 1 / (2 tau + 1), tau >= 0 */
+  lbm_bc face[6];     /* -x, +x, -y, +y, -z, +z.  This version accepts non-periodic kinds
+                         on the two x faces only; y and z must be periodic. */
+  int storage;        /* lbm_storage */
+  int fp64_moments;   /* 1: moment sums and temperature recovery in FP64 for FP32/FP16/BF16
+                         storage (no effect for LBM_F64); 0: FP32 */
+  void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
+                         creates its own stream (which synchronises with the legacy
+                         default stream) */
+} lbm_config;
+
+/* Device bytes lbm_create would allocate for this configuration (both population buffers
+ * and internal scratch).  Returns LBM_EINVAL for an invalid configuration. */
+lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes);
+
+/* Creates a context on the current CUDA device: validates cfg, allocates two population
+ * buffers.  On failure *out is NULL and lbm_last_error(NULL) tells why. */
+lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
+
+/* Sets every site's populations to f~eq(rho, u, theta) (App. B).  Fields as described
+ * above; they must be finite with rho > 0 and theta > 0 (not checked element-wise: a bad
+ * value shows up as LBM_EUNSTABLE later).  Also writes the equilibrium-inflow ghost layers.
+ * With on_device = 0 the call returns after the host data has been consumed. */
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, int on_device);
+
+/* Advances n >= 0 time steps: per step, zero-gradient ghost fills (if any) then one fused
+ * pull-stream-collide kernel over all sites.  Stream-ordered: returns once the work is
+ * queued.  Returns LBM_EINVAL if lbm_init / lbm_set_populations was never called. */
+lbm_status lbm_step(lbm_ctx* ctx, long long n);
+
+/* rho, u, theta of the stored (post-collision) state, computed in FP64 (Eq. (conslaws));
+ * layout as for lbm_init.  Synchronises the stream; returns LBM_EUNSTABLE (after writing
+ * the fields) if any step so far was flagged. */
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int on_device);
+
+/* Global sums over all sites of rho, rho u_x, rho u_y, rho u_z and <f, c^2>, FP64,
+ * bitwise reproducible for a given state (fixed reduction order).  out5: host double[5].
+ * Synchronises. */
+lbm_status lbm_totals(lbm_ctx* ctx, double* out5);
+
+/* Copies the populations out as dense FP64 f[sub][i][z][y][x] (2*81*nx*ny*nz values),
+ * decoding offset storage (f = w_i (1 + d_i)).  Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, int on_device);
+
+/* Sets the populations from dense FP64 f[sub][i][z][y][x] (encoding to the storage type).
+ * Also writes the equilibrium-inflow ghost layers.  Synchronises. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, int on_device);
+
+/* Gathers the 81 populations (FP64, decoded, library direction order) of `count` sites:
+ * f[k*81 + i] for site index sites[k] (0 <= sites[k] < 2*nx*ny*nz, field layout order).
+ * Host arrays.  Out-of-range indices give LBM_EINVAL before any work.  Synchronises. */
+lbm_status lbm_probe(lbm_ctx* ctx, const long long* sites, long long count, double* f);
+
+/* Waits for the context's queued work; LBM_EUNSTABLE if any step so far was flagged. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Number of kernel launches the context has issued so far (host-side count; every step
+ * issues 1 fused kernel plus 1 per zero-gradient face). */
+lbm_status lbm_launch_count(const lbm_ctx* ctx, long long* count);
+
+/* Frees the context and its device memory (after waiting for its queued work). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure on ctx, or of the last failed lbm_create on this thread when
+ * ctx is NULL.  Never NULL; valid until the next call on the same context / thread. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* The library's velocity set: h[3*i + a] = 2 c_{i,a} (integers) and w[i] = w_i, for the
+ * 81 directions in the library's order (rest first, then +v/-v pairs shell by shell as in
+ * Table "tab:weights").  Either pointer may be NULL.  Returns 81. */
+int lbm_velocities(int* h, double* w);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_RD3Q81_H */

@@ -1,0 +1,464 @@
+// C-ABI of liblbm_rd3q81 (declared and documented in include/lbm.h): context lifetime,
+// validation, device memory, chunked host transfers and the step loop.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "lbm.h"
+#include "device_common.cuh"
+
+namespace {
+
+constexpr uint32_t kMagic = 0x52443831u;  // "RD81"
+constexpr long long kChunkSites = 1LL << 22;  // sites per host-transfer chunk
+
+thread_local std::string g_create_error = "no error";
+
+long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  uint32_t magic = kMagic;
+  lbm_config cfg{};
+  lbm::Geometry g{};
+  lbm::LatticeTables tab{};
+  int storage = 0;
+  size_t elem = 0;
+  long long sites = 0;  // 2 * nx * ny * nz
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  unsigned int* d_flag = nullptr;
+  double* d_scratch = nullptr;
+  long long chunk = 0;
+  double* d_partials = nullptr;
+  double* d_totals = nullptr;
+  int totals_nb = 0;
+  double omega = 0.0;
+  bool initialized = false;
+  bool zero_grad[2] = {false, false};
+  bool inflow[2] = {false, false};
+  lbm::Feq81 feq_in[2]{};
+  long long launches = 0;
+  std::string err = "no error";
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define LBM_CK(ctx, call)                                                                       \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(ctx, LBM_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_));  \
+  } while (0)
+
+bool valid(const lbm_ctx* ctx) { return ctx != nullptr && ctx->magic == kMagic; }
+
+// Validates cfg and derives the buffer geometry; returns LBM_OK or LBM_EINVAL with *why.
+lbm_status plan(const lbm_config* cfg, lbm::Geometry* g, std::string* why) {
+  if (!cfg) return *why = "config is NULL", LBM_EINVAL;
+  if (cfg->velset != LBM_RD3Q81) return *why = "velset must be LBM_RD3Q81", LBM_EINVAL;
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return *why = "nx, ny, nz must be >= 1", LBM_EINVAL;
+  if (!(std::isfinite(cfg->tau) && cfg->tau >= 0.0)) return *why = "tau must be finite and >= 0", LBM_EINVAL;
+  if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return *why = "unknown storage", LBM_EINVAL;
+  if (cfg->fp64_moments != 0 && cfg->fp64_moments != 1) return *why = "fp64_moments must be 0 or 1", LBM_EINVAL;
+  for (int f = 0; f < 6; ++f) {
+    const lbm_bc& b = cfg->face[f];
+    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
+    if (f >= 2 && b.kind != LBM_BC_PERIODIC)
+      return *why = "only the x faces may be non-periodic in this version", LBM_EINVAL;
+    if (b.kind == LBM_BC_EQ_INFLOW &&
+        !(std::isfinite(b.rho) && b.rho > 0 && std::isfinite(b.theta) && b.theta > 0 &&
+          std::isfinite(b.ux) && std::isfinite(b.uy) && std::isfinite(b.uz)))
+      return *why = "inflow state needs finite u, rho > 0, theta > 0", LBM_EINVAL;
+  }
+  const bool xp0 = cfg->face[0].kind == LBM_BC_PERIODIC, xp1 = cfg->face[1].kind == LBM_BC_PERIODIC;
+  if (xp0 != xp1) return *why = "a periodic x face must be paired with a periodic x face", LBM_EINVAL;
+  const long long n = static_cast<long long>(cfg->nx) * cfg->ny * cfg->nz;
+  if (n >= (1LL << 31)) return *why = "nx*ny*nz must be < 2^31", LBM_EINVAL;
+
+  const long long elem = static_cast<long long>(lbm::storage_bytes(cfg->storage));
+  g->nx = cfg->nx;
+  g->ny = cfg->ny;
+  g->nz = cfg->nz;
+  g->x_periodic = xp0 ? 1 : 0;
+  if (xp0) {
+    g->xoff = 0;
+    g->pitch = cfg->nx;
+  } else {
+    // Ghost layers; the interior row starts on a 128-byte boundary.
+    const long long align = 128 / elem;
+    g->xoff = static_cast<int>(align);
+    const long long pitch = round_up(align + cfg->nx + rd3q81::kReach, align);
+    if (pitch >= (1LL << 31)) return *why = "row too long", LBM_EINVAL;
+    g->pitch = static_cast<int>(pitch);
+  }
+  g->plane = static_cast<long long>(g->pitch) * cfg->ny;
+  const long long slab = g->plane * cfg->nz;
+  if (slab >= (1LL << 31)) return *why = "one direction slab must hold < 2^31 elements", LBM_EINVAL;
+  g->dir_stride = round_up(slab, 64);
+  g->sub_stride = lbm::kQ * g->dir_stride;
+  return LBM_OK;
+}
+
+size_t buffer_bytes(const lbm::Geometry& g, int storage) {
+  return static_cast<size_t>(2 * g.sub_stride) * lbm::storage_bytes(storage);
+}
+
+long long chunk_sites(long long sites) { return sites < kChunkSites ? sites : kChunkSites; }
+
+// Scratch doubles: 5 fields per chunk site, and room for at least 256 probed sites.
+long long scratch_doubles(long long sites) {
+  const long long a = 5 * chunk_sites(sites), b = 256 * (1 + lbm::kQ);
+  return a > b ? a : b;
+}
+size_t scratch_bytes(long long sites) { return static_cast<size_t>(scratch_doubles(sites)) * sizeof(double); }
+
+size_t aux_bytes(const lbm::Geometry& g) {
+  return static_cast<size_t>(lbm::totals_blocks(g)) * 5 * sizeof(double) + 8 * sizeof(double) + 256;
+}
+
+lbm_status fill_inflow_faces(lbm_ctx* ctx) {
+  for (int face = 0; face < 2; ++face) {
+    if (!ctx->inflow[face]) continue;
+    for (int b = 0; b < 2; ++b) {
+      LBM_CK(ctx, lbm::launch_fill_inflow(ctx->storage, ctx->g, ctx->tab, ctx->buf[b], face,
+                                          ctx->feq_in[face], ctx->stream));
+      ++ctx->launches;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status check_flag(lbm_ctx* ctx) {
+  unsigned int flag = 0;
+  LBM_CK(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, ctx->stream));
+  LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  if (flag) return fail(ctx, LBM_EUNSTABLE, "a site saw rho <= 0, theta <= 0 or a non-finite value");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes) {
+  lbm::Geometry g;
+  std::string why;
+  if (!bytes) return fail(nullptr, LBM_EINVAL, "bytes is NULL");
+  if (plan(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+  const long long sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
+  *bytes = 2 * buffer_bytes(g, cfg->storage) + scratch_bytes(sites) + aux_bytes(g);
+  return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  lbm::Geometry g;
+  std::string why;
+  if (plan(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+
+  lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
+  if (!ctx) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+  ctx->cfg = *cfg;
+  ctx->g = g;
+  ctx->storage = cfg->storage;
+  ctx->elem = lbm::storage_bytes(cfg->storage);
+  ctx->sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
+  ctx->chunk = chunk_sites(ctx->sites);
+  ctx->omega = 2.0 / (2.0 * cfg->tau + 1.0);
+  lbm::build_lattice_tables(&ctx->tab);
+  for (int face = 0; face < 2; ++face) {
+    const lbm_bc& b = cfg->face[face];
+    ctx->zero_grad[face] = b.kind == LBM_BC_ZERO_GRADIENT;
+    ctx->inflow[face] = b.kind == LBM_BC_EQ_INFLOW;
+    if (ctx->inflow[face]) lbm::equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
+  }
+
+  auto bail = [&](lbm_status st, const std::string& msg) {
+    lbm_destroy(ctx);
+    return fail(nullptr, st, msg);
+  };
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e != cudaSuccess) return bail(LBM_ECUDA, std::string("cudaGetDevice failed: ") + cudaGetErrorString(e));
+  if (cfg->cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    e = cudaStreamCreate(&ctx->stream);
+    if (e != cudaSuccess) return bail(LBM_ECUDA, std::string("cudaStreamCreate failed: ") + cudaGetErrorString(e));
+    ctx->own_stream = true;
+  }
+  const size_t bb = buffer_bytes(g, ctx->storage);
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&ctx->buf[b], bb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(LBM_ENOMEM, "cudaMalloc of a population buffer (" + std::to_string(bb) + " bytes) failed: " +
+                                  cudaGetErrorString(e));
+    }
+  }
+  ctx->totals_nb = lbm::totals_blocks(g);
+  e = cudaMalloc(&ctx->d_scratch, scratch_bytes(ctx->sites));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_partials, ctx->totals_nb * 5 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_totals, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flag, 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, 256, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(LBM_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, int on_device) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!rho || !u || !theta) return fail(ctx, LBM_EINVAL, "NULL field pointer");
+  DeviceGuard dg(ctx->device);
+  const long long S = ctx->sites;
+  ctx->cur = 0;
+  if (on_device) {
+    LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], rho, u, theta, 0, S, S, ctx->stream));
+    ++ctx->launches;
+  } else {
+    double* sr = ctx->d_scratch;
+    double* su = sr + ctx->chunk;
+    double* st = su + 3 * ctx->chunk;
+    for (long long first = 0; first < S; first += ctx->chunk) {
+      const long long cnt = S - first < ctx->chunk ? S - first : ctx->chunk;
+      const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
+      LBM_CK(ctx, cudaMemcpyAsync(sr, rho + first, nb, cudaMemcpyHostToDevice, ctx->stream));
+      for (int a = 0; a < 3; ++a)
+        LBM_CK(ctx, cudaMemcpyAsync(su + a * cnt, u + a * S + first, nb, cudaMemcpyHostToDevice, ctx->stream));
+      LBM_CK(ctx, cudaMemcpyAsync(st, theta + first, nb, cudaMemcpyHostToDevice, ctx->stream));
+      LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], sr, su, st, first, cnt, cnt,
+                                   ctx->stream));
+      ++ctx->launches;
+    }
+  }
+  lbm_status st = fill_inflow_faces(ctx);
+  if (st != LBM_OK) return st;
+  LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
+  if (!on_device) LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, long long n) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  lbm::StepParams p;
+  p.g = ctx->g;
+  p.omega = ctx->omega;
+  p.flag = ctx->d_flag;
+  p.tab = ctx->tab;
+  for (long long k = 0; k < n; ++k) {
+    for (int face = 0; face < 2; ++face) {
+      if (!ctx->zero_grad[face]) continue;
+      LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
+      ++ctx->launches;
+    }
+    p.src = ctx->buf[ctx->cur];
+    p.dst = ctx->buf[ctx->cur ^ 1];
+    LBM_CK(ctx, lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, p, ctx->stream));
+    ++ctx->launches;
+    ctx->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int on_device) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!rho || !u || !theta) return fail(ctx, LBM_EINVAL, "NULL field pointer");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  const long long S = ctx->sites;
+  const void* b = ctx->buf[ctx->cur];
+  if (on_device) {
+    LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, rho, u, theta, 0, S, S, ctx->stream));
+    ++ctx->launches;
+  } else {
+    double* sr = ctx->d_scratch;
+    double* su = sr + ctx->chunk;
+    double* st = su + 3 * ctx->chunk;
+    for (long long first = 0; first < S; first += ctx->chunk) {
+      const long long cnt = S - first < ctx->chunk ? S - first : ctx->chunk;
+      const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
+      LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, sr, su, st, first, cnt, cnt, ctx->stream));
+      ++ctx->launches;
+      LBM_CK(ctx, cudaMemcpyAsync(rho + first, sr, nb, cudaMemcpyDeviceToHost, ctx->stream));
+      for (int a = 0; a < 3; ++a)
+        LBM_CK(ctx, cudaMemcpyAsync(u + a * S + first, su + a * cnt, nb, cudaMemcpyDeviceToHost, ctx->stream));
+      LBM_CK(ctx, cudaMemcpyAsync(theta + first, st, nb, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  return check_flag(ctx);
+}
+
+lbm_status lbm_totals(lbm_ctx* ctx, double* out5) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!out5) return fail(ctx, LBM_EINVAL, "out5 is NULL");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  LBM_CK(ctx, lbm::launch_totals(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], ctx->d_partials,
+                                 ctx->totals_nb, ctx->d_totals, ctx->stream));
+  ctx->launches += 2;
+  LBM_CK(ctx, cudaMemcpyAsync(out5, ctx->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, int on_device) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!f) return fail(ctx, LBM_EINVAL, "f is NULL");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  const long long total = ctx->sites * lbm::kQ;
+  const void* b = ctx->buf[ctx->cur];
+  if (on_device) {
+    LBM_CK(ctx, lbm::launch_get_populations(ctx->storage, ctx->g, ctx->tab, b, f, 0, total, ctx->stream));
+    ++ctx->launches;
+  } else {
+    const long long ck = 5 * ctx->chunk;
+    for (long long first = 0; first < total; first += ck) {
+      const long long cnt = total - first < ck ? total - first : ck;
+      LBM_CK(ctx, lbm::launch_get_populations(ctx->storage, ctx->g, ctx->tab, b, ctx->d_scratch, first, cnt,
+                                              ctx->stream));
+      ++ctx->launches;
+      LBM_CK(ctx, cudaMemcpyAsync(f + first, ctx->d_scratch, static_cast<size_t>(cnt) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    }
+  }
+  LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, int on_device) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!f) return fail(ctx, LBM_EINVAL, "f is NULL");
+  DeviceGuard dg(ctx->device);
+  const long long total = ctx->sites * lbm::kQ;
+  ctx->cur = 0;
+  if (on_device) {
+    LBM_CK(ctx, lbm::launch_set_populations(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], f, 0, total, ctx->stream));
+    ++ctx->launches;
+  } else {
+    const long long ck = 5 * ctx->chunk;
+    for (long long first = 0; first < total; first += ck) {
+      const long long cnt = total - first < ck ? total - first : ck;
+      LBM_CK(ctx, cudaMemcpyAsync(ctx->d_scratch, f + first, static_cast<size_t>(cnt) * sizeof(double),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+      LBM_CK(ctx, lbm::launch_set_populations(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], ctx->d_scratch, first,
+                                              cnt, ctx->stream));
+      ++ctx->launches;
+    }
+  }
+  lbm_status st = fill_inflow_faces(ctx);
+  if (st != LBM_OK) return st;
+  LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
+  LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->initialized = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_probe(lbm_ctx* ctx, const long long* sites, long long count, double* f) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (count < 0 || (count > 0 && (!sites || !f))) return fail(ctx, LBM_EINVAL, "bad probe arguments");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  for (long long k = 0; k < count; ++k)
+    if (sites[k] < 0 || sites[k] >= ctx->sites) return fail(ctx, LBM_EINVAL, "probe site index out of range");
+  DeviceGuard dg(ctx->device);
+  // Scratch holds 5 * chunk doubles: site indices (as 64-bit integers) and then the values.
+  const long long per = scratch_doubles(ctx->sites) / (1 + lbm::kQ);
+  long long* d_sites = reinterpret_cast<long long*>(ctx->d_scratch);
+  double* d_vals = ctx->d_scratch + per;
+  for (long long first = 0; first < count; first += per) {
+    const long long cnt = count - first < per ? count - first : per;
+    LBM_CK(ctx, cudaMemcpyAsync(d_sites, sites + first, cnt * sizeof(long long), cudaMemcpyHostToDevice,
+                                ctx->stream));
+    LBM_CK(ctx, lbm::launch_probe(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], d_sites, cnt, d_vals,
+                                  ctx->stream));
+    ++ctx->launches;
+    LBM_CK(ctx, cudaMemcpyAsync(f + first * lbm::kQ, d_vals, cnt * lbm::kQ * sizeof(double),
+                                cudaMemcpyDeviceToHost, ctx->stream));
+    LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx* ctx) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  DeviceGuard dg(ctx->device);
+  return check_flag(ctx);
+}
+
+lbm_status lbm_launch_count(const lbm_ctx* ctx, long long* count) {
+  if (!valid(ctx) || !count) return LBM_EINVAL;
+  *count = ctx->launches;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* ctx) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  {
+    DeviceGuard dg(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int b = 0; b < 2; ++b)
+      if (ctx->buf[b]) cudaFree(ctx->buf[b]);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    if (ctx->d_partials) cudaFree(ctx->d_partials);
+    if (ctx->d_totals) cudaFree(ctx->d_totals);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  }
+  ctx->magic = 0;
+  delete ctx;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+  if (ctx == nullptr) return g_create_error.c_str();
+  if (!valid(ctx)) return "invalid context";
+  return ctx->err.c_str();
+}
+
+int lbm_velocities(int* h, double* w) {
+  lbm::LatticeTables t;
+  lbm::build_lattice_tables(&t);
+  for (int i = 0; i < lbm::kQ; ++i) {
+    if (h) {
+      h[3 * i + 0] = rd3q81::kDirs[i].hx;
+      h[3 * i + 1] = rd3q81::kDirs[i].hy;
+      h[3 * i + 2] = rd3q81::kDirs[i].hz;
+    }
+    if (w) w[i] = t.wdir[i];
+  }
+  return lbm::kQ;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+// Auxiliary kernels around the fused step: initialisation from macroscopic fields, moment
+// read-back, raw population get/set (FP64, dense layout), boundary ghost layers, and the
+// deterministic global conservation sums.
+#include "device_common.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kAuxBlock = 256;
+
+// Element offset of interior site t (0 <= t < nx*ny*nz) of sublattice `sub`, direction 0.
+__device__ __forceinline__ long long site_offset(const Geometry& g, int sub, long long t) {
+  const int x = static_cast<int>(t % g.nx);
+  const long long r = t / g.nx;
+  const int y = static_cast<int>(r % g.ny);
+  const int z = static_cast<int>(r / g.ny);
+  return sub * g.sub_stride + z * g.plane + static_cast<long long>(y) * g.pitch + g.xoff + x;
+}
+
+template <class S>
+__device__ __forceinline__ double decode(S v, double w) {
+  if constexpr (Codec<S>::kOffset) {
+    return w * (1.0 + static_cast<double>(Codec<S>::load(&v)));
+  } else {
+    return static_cast<double>(v);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ void encode(S* p, double f, double w) {
+  if constexpr (Codec<S>::kOffset) {
+    Codec<S>::store(p, static_cast<float>(f / w - 1.0));
+  } else {
+    *p = static_cast<S>(f);
+  }
+}
+
+template <class S>
+__global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double* rho, const double* u,
+                            const double* theta, long long first, long long count, long long us) {
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= count) return;
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  const long long gs = first + k;
+  const int sub = gs >= n ? 1 : 0;
+  const long long off = site_offset(g, sub, gs - sub * n);
+  double feq[kQ];
+  equilibrium_f64(rho[k], u[k], u[us + k], u[2 * us + k], theta[k], tab, feq);
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    encode<S>(buf + off + i * g.dir_stride, feq[i], tab.w[rd3q81::kDirs[i].shell]);
+  });
+}
+
+// Moments of the stored populations in FP64 (Eq. (conslaws)); for offset storage as
+// deviations from the weights' own moments (1, 0, 3 theta0).
+template <class S>
+__device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTables& tab, const S* buf,
+                                             long long off, double& rho, double& jx, double& jy,
+                                             double& jz, double& e) {
+  rho = jx = jy = jz = e = 0.0;
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[i];
+    constexpr double c2 = rd3q81::kShellC2[d.shell];
+    const S v = buf[off + i * g.dir_stride];
+    double f;
+    if constexpr (Codec<S>::kOffset)
+      f = tab.w[d.shell] * static_cast<double>(Codec<S>::load(&v));
+    else
+      f = static_cast<double>(v);
+    rho += f;
+    e += c2 * f;
+    if constexpr (d.hx != 0) jx += 0.5 * d.hx * f;
+    if constexpr (d.hy != 0) jy += 0.5 * d.hy * f;
+    if constexpr (d.hz != 0) jz += 0.5 * d.hz * f;
+  });
+  if constexpr (Codec<S>::kOffset) {
+    rho += 1.0;
+    e += 3.0 * tab.theta0;
+  }
+}
+
+template <class S>
+__global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, double* rho, double* u,
+                               double* theta, long long first, long long count, long long us) {
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= count) return;
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  const long long gs = first + k;
+  const int sub = gs >= n ? 1 : 0;
+  double r, jx, jy, jz, e;
+  site_moments<S>(g, tab, buf, site_offset(g, sub, gs - sub * n), r, jx, jy, jz, e);
+  const double ux = jx / r, uy = jy / r, uz = jz / r;
+  rho[k] = r;
+  u[k] = ux;
+  u[us + k] = uy;
+  u[2 * us + k] = uz;
+  theta[k] = (e / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+}
+
+// Dense FP64 layout f[sub][i][z][y][x] <-> padded storage.
+// Dense element k = (sub*81 + i)*n + t; the kernels handle k in [first, first + count)
+// with f pointing at element `first`.
+template <class S>
+__global__ void get_pop_kernel(Geometry g, LatticeTables tab, const S* buf, double* f, long long first,
+                               long long count) {
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (j >= count) return;
+  const long long k = first + j;
+  const long long t = k % n;
+  const int i = static_cast<int>((k / n) % kQ);
+  const int sub = static_cast<int>(k / (n * kQ));
+  f[j] = decode<S>(buf[site_offset(g, sub, t) + i * g.dir_stride], tab.wdir[i]);
+}
+
+template <class S>
+__global__ void set_pop_kernel(Geometry g, LatticeTables tab, S* buf, const double* f, long long first,
+                               long long count) {
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (j >= count) return;
+  const long long k = first + j;
+  const long long t = k % n;
+  const int i = static_cast<int>((k / n) % kQ);
+  const int sub = static_cast<int>(k / (n * kQ));
+  encode<S>(buf + site_offset(g, sub, t) + i * g.dir_stride, f[j], tab.wdir[i]);
+}
+
+// Populations of selected sites: thread per (sample, direction).
+template <class S>
+__global__ void probe_kernel(Geometry g, LatticeTables tab, const S* buf, const long long* sites,
+                             long long count, double* f) {
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (j >= count * kQ) return;
+  const long long k = j / kQ;
+  const int i = static_cast<int>(j % kQ);
+  const long long gs = sites[k];
+  const int sub = gs >= n ? 1 : 0;
+  f[j] = decode<S>(buf[site_offset(g, sub, gs - sub * n) + i * g.dir_stride], tab.wdir[i]);
+}
+
+// Ghost layers of one x face: thread per (sub, i, z, y) row.  Zero gradient copies the
+// nearest interior site of the same sublattice into all kReach layers; inflow writes feq.
+template <class S>
+__global__ void zero_gradient_kernel(Geometry g, S* buf, int face) {
+  const long long rows = 2LL * kQ * g.nz * g.ny;
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= rows) return;
+  const int y = static_cast<int>(k % g.ny);
+  const long long r = k / g.ny;
+  const int z = static_cast<int>(r % g.nz);
+  const long long si = r / g.nz;  // sub * kQ + i
+  const long long row = (si / kQ) * g.sub_stride + (si % kQ) * g.dir_stride + z * g.plane +
+                        static_cast<long long>(y) * g.pitch;
+  if (face == 0) {
+    const S v = buf[row + g.xoff];
+    for (int l = 1; l <= rd3q81::kReach; ++l) buf[row + g.xoff - l] = v;
+  } else {
+    const S v = buf[row + g.xoff + g.nx - 1];
+    for (int l = 0; l < rd3q81::kReach; ++l) buf[row + g.xoff + g.nx + l] = v;
+  }
+}
+
+template <class S>
+__global__ void inflow_kernel(Geometry g, LatticeTables tab, S* buf, int face, Feq81 feq) {
+  const long long rows = 2LL * kQ * g.nz * g.ny;
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= rows) return;
+  const int y = static_cast<int>(k % g.ny);
+  const long long r = k / g.ny;
+  const int z = static_cast<int>(r % g.nz);
+  const long long si = r / g.nz;
+  const int i = static_cast<int>(si % kQ);
+  const long long row = (si / kQ) * g.sub_stride + i * g.dir_stride + z * g.plane +
+                        static_cast<long long>(y) * g.pitch;
+  const long long x0 = face == 0 ? g.xoff - rd3q81::kReach : g.xoff + g.nx;
+  for (int l = 0; l < rd3q81::kReach; ++l) encode<S>(buf + row + x0 + l, feq.v[i], tab.wdir[i]);
+}
+
+// Global sums (rho, j_x, j_y, j_z, <f, c^2>) over all sites.  Pass 1: per-block partials
+// (fixed grid, fixed per-thread order); pass 2: one block sums them in a fixed order, so
+// the result is bitwise reproducible.
+template <class S>
+__global__ void totals_pass1(Geometry g, LatticeTables tab, const S* buf, double* partials) {
+  const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x; k < 2 * n;
+       k += static_cast<long long>(gridDim.x) * kAuxBlock) {
+    const int sub = k >= n ? 1 : 0;
+    double r, jx, jy, jz, e;
+    site_moments<S>(g, tab, buf, site_offset(g, sub, k - sub * n), r, jx, jy, jz, e);
+    acc[0] += r;
+    acc[1] += jx;
+    acc[2] += jy;
+    acc[3] += jz;
+    acc[4] += e;
+  }
+  __shared__ double sh[5][kAuxBlock];
+  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = kAuxBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void totals_pass2(const double* partials, int nblocks, double* out) {
+  if (threadIdx.x < 5) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kAuxBlock - 1) / kAuxBlock); }
+
+}  // namespace
+
+#define LBM_STORAGE_DISPATCH(storage, BODY)            \
+  switch (storage) {                                   \
+    case kF64: { using S = double; BODY; } break;      \
+    case kF32: { using S = float; BODY; } break;       \
+    case kF16Off: { using S = __half; BODY; } break;   \
+    case kBF16Off: { using S = __nv_bfloat16; BODY; } break; \
+    default: return cudaErrorInvalidValue;             \
+  }
+
+cudaError_t launch_init(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
+                        const double* rho, const double* u, const double* theta,
+                        long long first_site, long long count, long long u_stride, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  LBM_STORAGE_DISPATCH(storage, (init_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
+                           double* rho, double* u, double* theta, long long first_site,
+                           long long count, long long u_stride, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  LBM_STORAGE_DISPATCH(storage, (moments_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<const S*>(buf), rho, u, theta, first_site, count, u_stride)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(int storage, const Geometry& g, const LatticeTables& tab,
+                                   const void* buf, double* f, long long first, long long count,
+                                   cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  LBM_STORAGE_DISPATCH(storage, (get_pop_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<const S*>(buf), f, first, count)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
+                                   const double* f, long long first, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  LBM_STORAGE_DISPATCH(storage, (set_pop_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<S*>(buf), f, first, count)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s) {
+  const long long rows = 2LL * kQ * g.nz * g.ny;
+  LBM_STORAGE_DISPATCH(storage, (zero_gradient_kernel<S><<<blocks_for(rows), kAuxBlock, 0, s>>>(
+                                    g, static_cast<S*>(buf), face)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_inflow(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
+                               int face, const Feq81& feq, cudaStream_t s) {
+  const long long rows = 2LL * kQ * g.nz * g.ny;
+  LBM_STORAGE_DISPATCH(storage, (inflow_kernel<S><<<blocks_for(rows), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<S*>(buf), face, feq)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
+                         const long long* sites, long long count, double* f, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  LBM_STORAGE_DISPATCH(storage, (probe_kernel<S><<<blocks_for(count * kQ), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<const S*>(buf), sites, count, f)));
+  return cudaGetLastError();
+}
+
+int totals_blocks(const Geometry& g) {
+  const long long n = 2LL * g.nx * g.ny * g.nz;
+  const long long b = (n + kAuxBlock - 1) / kAuxBlock;
+  return static_cast<int>(b < 1024 ? b : 1024);
+}
+
+cudaError_t launch_totals(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
+                          double* partials, int nblocks, double* out5, cudaStream_t s) {
+  LBM_STORAGE_DISPATCH(storage, (totals_pass1<S><<<nblocks, kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<const S*>(buf), partials)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  totals_pass2<<<1, 32, 0, s>>>(partials, nblocks, out5);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide(int storage, int fp64_moments, const StepParams& p, cudaStream_t s) {
+  switch (storage) {
+    case kF64: return launch_sc_f64(fp64_moments, p, s);
+    case kF32: return launch_sc_f32(fp64_moments, p, s);
+    case kF16Off: return launch_sc_f16(fp64_moments, p, s);
+    case kBF16Off: return launch_sc_bf16(fp64_moments, p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lbm

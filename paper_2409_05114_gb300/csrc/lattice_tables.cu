@@ -1,0 +1,70 @@
+// Host-side construction of the lattice constants (FP64), from Table "tab:weights" and the
+// series temperature weights of App. B, Eq. (zeroveleqseries).
+#include "lbm_internal.h"
+
+namespace lbm {
+
+void build_lattice_tables(LatticeTables* t) {
+  using namespace rd3q81;
+  const double t0 = kTheta0;
+
+  // Shell weights: quintic polynomials in theta0 (Horner), w_0 = 1 - sum of the others.
+  double w[kShells];
+  double others = 0.0;
+  for (int s = 1; s < kShells; ++s) {
+    const WeightPoly& wp = kWeightPoly[s];
+    double acc = 0.0;
+    for (int k = 5; k >= 1; --k) acc = (acc + wp.num[k]) * t0;
+    w[s] = acc / wp.den;
+    others += kShellCount[s] * w[s];
+  }
+  w[0] = 1.0 - others;
+
+  // W~_s / (rho w_s) = 1 + eta/2 (y-3) + eta^2/8 (y^2-10y+15) + eta^3/48 (y^3-21y^2+105y-105)
+  //                    + eta^4/384 (y^4-36y^3+378y^2-1260y+945),   y = c_s^2 / theta0.
+  for (int s = 0; s < kShells; ++s) {
+    const double y = kShellC2[s] / t0;
+    const double y2 = y * y, y3 = y2 * y, y4 = y3 * y;
+    t->p[s][0] = 1.0;
+    t->p[s][1] = (y - 3.0) / 2.0;
+    t->p[s][2] = (y2 - 10.0 * y + 15.0) / 8.0;
+    t->p[s][3] = (y3 - 21.0 * y2 + 105.0 * y - 105.0) / 48.0;
+    t->p[s][4] = (y4 - 36.0 * y3 + 378.0 * y2 - 1260.0 * y + 945.0) / 384.0;
+    t->w[s] = w[s];
+    for (int k = 0; k < 5; ++k) t->wp[s][k] = w[s] * t->p[s][k];
+  }
+
+  // Coefficients (in eta) of <W~/rho, c_x^4> and <W~/rho, c_x^2 c_y^2>, summed over the 81
+  // directions, then the numerators of A and B over theta^2 = theta0^2 (1 + eta)^2.
+  double mxx[5] = {0, 0, 0, 0, 0}, mxy[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < kQ; ++i) {
+    const double cx = 0.5 * kDirs[i].hx, cy = 0.5 * kDirs[i].hy;
+    const int s = kDirs[i].shell;
+    for (int k = 0; k < 5; ++k) {
+      mxx[k] += t->wp[s][k] * cx * cx * cx * cx;
+      mxy[k] += t->wp[s][k] * cx * cx * cy * cy;
+    }
+  }
+  const double th2[5] = {t0 * t0, 2.0 * t0 * t0, t0 * t0, 0.0, 0.0};
+  for (int k = 0; k < 5; ++k) {
+    t->nb[k] = mxy[k] - th2[k];
+    t->na[k] = mxx[k] - 3.0 * mxy[k];
+  }
+  t->theta0 = t0;
+
+  for (int s = 0; s < kShells; ++s) {
+    t->wf[s] = static_cast<float>(t->w[s]);
+    for (int k = 0; k < 5; ++k) {
+      t->wpf[s][k] = static_cast<float>(t->wp[s][k]);
+      t->pf[s][k] = static_cast<float>(t->p[s][k]);
+    }
+  }
+  for (int k = 0; k < 5; ++k) {
+    t->naf[k] = static_cast<float>(t->na[k]);
+    t->nbf[k] = static_cast<float>(t->nb[k]);
+  }
+  t->theta0f = static_cast<float>(t0);
+  for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
+}
+
+}  // namespace lbm

@@ -1,0 +1,11 @@
+// Fused stream-collide instantiations for __half storage (one translation unit per storage
+// type so that they compile in parallel).
+#include "stream_collide.cuh"
+
+namespace lbm {
+
+cudaError_t launch_sc_f16(int fp64_moments, const StepParams& p, cudaStream_t s) {
+  return fp64_moments ? launch_sc<__half, true>(p, s) : launch_sc<__half, false>(p, s);
+}
+
+}  // namespace lbm

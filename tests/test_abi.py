@@ -1,0 +1,100 @@
+"""The C-ABI library (CPU-side checks, no device compute): it builds, loads, exports every
+entry point include/lbm.h declares, reports the RD3Q81 velocity set the oracle builds
+independently, and validates configurations on the host (lbm_footprint)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from parity_util import ROOT, ensure_built, lib_perm
+from oracle import rd3q81 as O
+
+
+@pytest.fixture(scope="module")
+def B():
+    ensure_built()
+    from paper_2409_05114_gb300 import binding
+    return binding
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(B):
+    import ctypes
+    lib = ctypes.CDLL(B.library_path())
+    names = _declared()
+    assert len(names) >= 13
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_velocity_set_matches_oracle(B):
+    h, w = B.lbm_velocities()
+    lat = O.velocity_set()
+    perm = lib_perm()
+    assert sorted(perm.tolist()) == list(range(81))
+    np.testing.assert_array_equal(h, lat.h[perm])
+    np.testing.assert_allclose(w, lat.w[perm], rtol=1e-13, atol=0)  # FP64 Horner of the table rows
+    # +/- pairs are adjacent: direction 2k is -direction 2k-1
+    np.testing.assert_array_equal(h[2::2], -h[1::2])
+
+
+def _cfg(B, **kw):
+    args = dict(nx=16, ny=8, nz=4, tau=0.1, storage="f32")
+    args.update(kw)
+    faces = args.pop("faces", None)
+    return B.make_config(faces=faces, **args)
+
+
+def test_footprint_and_padding(B):
+    n = 64 * 32 * 8
+    fp = B.lbm_footprint(_cfg(B, nx=64, ny=32, nz=8))
+    assert fp >= 2 * 2 * 81 * n * 4
+    assert fp < 2 * 2 * 81 * n * 4 * 1.05 + (64 << 20)
+    fp16 = B.lbm_footprint(_cfg(B, nx=64, ny=32, nz=8, storage="f16"))
+    fp64 = B.lbm_footprint(_cfg(B, nx=64, ny=32, nz=8, storage="f64"))
+    assert fp16 < fp < fp64
+    # non-periodic x adds aligned ghost layers
+    fz = B.lbm_footprint(_cfg(B, nx=64, ny=32, nz=8, faces=["zero_gradient", "zero_gradient"]))
+    assert fz > fp
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(ny=-1), dict(tau=-0.1), dict(tau=float("nan")), dict(storage=7),
+    dict(faces=["periodic", "zero_gradient"]),
+    dict(faces=["periodic", "periodic", "zero_gradient"]),
+    dict(faces=[("eq_inflow", -1.0, 0, 0, 0, 0.8), "zero_gradient"]),
+    dict(faces=[("eq_inflow", 1.0, 0, 0, 0, 0.0), "zero_gradient"]),
+    dict(nx=2048, ny=2048, nz=1024),
+])
+def test_invalid_configs_rejected(B, bad):
+    with pytest.raises(B.LbmError) as ei:
+        B.lbm_footprint(_cfg(B, **bad))
+    assert ei.value.status == B.LBM_EINVAL
+    assert B.lbm_last_error(None) != "no error"
+
+
+def test_bad_face_kind_rejected(B):
+    cfg = _cfg(B)
+    cfg.face[0].kind = 9
+    with pytest.raises(B.LbmError):
+        B.lbm_footprint(cfg)
+    cfg = _cfg(B)
+    cfg.velset = 2
+    with pytest.raises(B.LbmError):
+        B.lbm_footprint(cfg)
+
+
+def test_null_context_calls_are_einval(B):
+    import ctypes
+    lib = B._lib
+    assert lib.lbm_step(None, 1) == B.LBM_EINVAL
+    assert lib.lbm_sync(None) == B.LBM_EINVAL
+    assert lib.lbm_destroy(None) == B.LBM_EINVAL
+    assert lib.lbm_totals(None, None) == B.LBM_EINVAL
+    assert lib.lbm_last_error(None) is not None
