@@ -155,6 +155,61 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * Table "tab:weights").  Either pointer may be NULL.  Returns 81. */
 int lbm_velocities(int* h, double* w);
 
+/* ---- serving: continuous batching of independent cases on one GPU --------------------
+ *
+ * A server keeps many cases (each an lbm_config with its own grid, tau, faces and storage)
+ * resident on the current device and advances all of them together: every time step is
+ * one persistent fused kernel over a packed index of all resident sites (plus one batched
+ * zero-gradient fill if any resident case needs it), and runs of up to 16 steps are
+ * replayed as CUDA graphs.  Requests are admitted in submission order whenever a slot is
+ * free and the sum of resident case footprints (2 population buffers each) stays within
+ * the HBM budget; admission (host-to-device copy and initialisation) runs on its own
+ * stream while the resident cases compute.  A case leaves after its step count, or early
+ * when one of its sites becomes unstable.  Its result is bitwise the same as when it runs
+ * alone: every site is updated by the same code as lbm_step.  A scheduler thread owned by
+ * the server does all GPU work; the calls below are thread-safe. */
+typedef struct lbm_server lbm_server;
+
+typedef struct {
+  long long submitted, admitted, completed, unstable, rejected, queued;
+  long long site_updates;           /* sum of sites x steps over cases completed OK */
+  long long ticks, kernel_launches, graph_launches;
+  int resident_cases;
+  size_t resident_bytes, peak_resident_bytes;
+  double busy_seconds;              /* scheduler time spent running ticks */
+} lbm_server_stats;
+
+/* Creates a server on the current device.  hbm_budget_bytes bounds the resident cases'
+ * population memory (the server adds ~170 MB of staging of its own); 1 <= max_cases <= 1024. */
+lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server** out);
+
+/* Queues one case: configuration (storage FP32, FP16 or BF16 offsets, fp64_moments = 0;
+ * cuda_stream is ignored), initial fields in host memory (layout as lbm_init; copied
+ * before the call returns) and nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case
+ * alone exceeds the budget, LBM_EINVAL for an invalid configuration. */
+lbm_status lbm_submit(lbm_server* srv, const lbm_config* cfg, const double* rho, const double* u,
+                      const double* theta, long long nsteps, long long* ticket);
+
+/* Non-blocking.  LBM_EBUSY while the case is queued or running; once it is done, copies
+ * rho, u, theta (host arrays, layout as lbm_moments; any may be NULL) and the time from
+ * submission to completion, returns the case's status (LBM_OK or LBM_EUNSTABLE) and
+ * forgets the ticket (LBM_ENOTFOUND afterwards). */
+lbm_status lbm_poll(lbm_server* srv, long long ticket, double* rho, double* u, double* theta,
+                    double* latency_s);
+
+/* Blocks until the case is done (LBM_OK, then lbm_poll for the result) or timeout_s
+ * seconds passed (LBM_ETIMEOUT). */
+lbm_status lbm_wait(lbm_server* srv, long long ticket, double timeout_s);
+
+lbm_status lbm_server_get_stats(lbm_server* srv, lbm_server_stats* out);
+
+/* Message of the server's last failure (or of the last failed lbm_server_create when srv
+ * is NULL). */
+const char* lbm_server_last_error(const lbm_server* srv);
+
+/* Stops the scheduler (queued and running cases are dropped) and frees everything. */
+lbm_status lbm_server_destroy(lbm_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,56 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace lbm {
+
+lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
+  if (!cfg) return *why = "config is NULL", LBM_EINVAL;
+  if (cfg->velset != LBM_RD3Q81) return *why = "velset must be LBM_RD3Q81", LBM_EINVAL;
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return *why = "nx, ny, nz must be >= 1", LBM_EINVAL;
+  if (!(std::isfinite(cfg->tau) && cfg->tau >= 0.0)) return *why = "tau must be finite and >= 0", LBM_EINVAL;
+  if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return *why = "unknown storage", LBM_EINVAL;
+  if (cfg->fp64_moments != 0 && cfg->fp64_moments != 1) return *why = "fp64_moments must be 0 or 1", LBM_EINVAL;
+  for (int f = 0; f < 6; ++f) {
+    const lbm_bc& b = cfg->face[f];
+    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
+    if (f >= 2 && b.kind != LBM_BC_PERIODIC)
+      return *why = "only the x faces may be non-periodic in this version", LBM_EINVAL;
+    if (b.kind == LBM_BC_EQ_INFLOW &&
+        !(std::isfinite(b.rho) && b.rho > 0 && std::isfinite(b.theta) && b.theta > 0 &&
+          std::isfinite(b.ux) && std::isfinite(b.uy) && std::isfinite(b.uz)))
+      return *why = "inflow state needs finite u, rho > 0, theta > 0", LBM_EINVAL;
+  }
+  const bool xp0 = cfg->face[0].kind == LBM_BC_PERIODIC, xp1 = cfg->face[1].kind == LBM_BC_PERIODIC;
+  if (xp0 != xp1) return *why = "a periodic x face must be paired with a periodic x face", LBM_EINVAL;
+  const long long n = static_cast<long long>(cfg->nx) * cfg->ny * cfg->nz;
+  if (n >= (1LL << 31)) return *why = "nx*ny*nz must be < 2^31", LBM_EINVAL;
+
+  const long long elem = static_cast<long long>(storage_bytes(cfg->storage));
+  g->nx = cfg->nx;
+  g->ny = cfg->ny;
+  g->nz = cfg->nz;
+  g->x_periodic = xp0 ? 1 : 0;
+  if (xp0) {
+    g->xoff = 0;
+    g->pitch = cfg->nx;
+  } else {
+    // Ghost layers; the interior row starts on a 128-byte boundary.
+    const long long align = 128 / elem;
+    g->xoff = static_cast<int>(align);
+    const long long pitch = round_up(align + cfg->nx + rd3q81::kReach, align);
+    if (pitch >= (1LL << 31)) return *why = "row too long", LBM_EINVAL;
+    g->pitch = static_cast<int>(pitch);
+  }
+  g->plane = static_cast<long long>(g->pitch) * cfg->ny;
+  const long long slab = g->plane * cfg->nz;
+  if (slab >= (1LL << 31)) return *why = "one direction slab must hold < 2^31 elements", LBM_EINVAL;
+  g->dir_stride = round_up(slab, 64);
+  g->sub_stride = kQ * g->dir_stride;
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
 struct lbm_ctx {
   uint32_t magic = kMagic;
   lbm_config cfg{};
@@ -75,53 +125,6 @@ lbm_status fail(lbm_ctx* ctx, lbm_status st, const std::string& msg) {
   } while (0)
 
 bool valid(const lbm_ctx* ctx) { return ctx != nullptr && ctx->magic == kMagic; }
-
-// Validates cfg and derives the buffer geometry; returns LBM_OK or LBM_EINVAL with *why.
-lbm_status plan(const lbm_config* cfg, lbm::Geometry* g, std::string* why) {
-  if (!cfg) return *why = "config is NULL", LBM_EINVAL;
-  if (cfg->velset != LBM_RD3Q81) return *why = "velset must be LBM_RD3Q81", LBM_EINVAL;
-  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return *why = "nx, ny, nz must be >= 1", LBM_EINVAL;
-  if (!(std::isfinite(cfg->tau) && cfg->tau >= 0.0)) return *why = "tau must be finite and >= 0", LBM_EINVAL;
-  if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return *why = "unknown storage", LBM_EINVAL;
-  if (cfg->fp64_moments != 0 && cfg->fp64_moments != 1) return *why = "fp64_moments must be 0 or 1", LBM_EINVAL;
-  for (int f = 0; f < 6; ++f) {
-    const lbm_bc& b = cfg->face[f];
-    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
-    if (f >= 2 && b.kind != LBM_BC_PERIODIC)
-      return *why = "only the x faces may be non-periodic in this version", LBM_EINVAL;
-    if (b.kind == LBM_BC_EQ_INFLOW &&
-        !(std::isfinite(b.rho) && b.rho > 0 && std::isfinite(b.theta) && b.theta > 0 &&
-          std::isfinite(b.ux) && std::isfinite(b.uy) && std::isfinite(b.uz)))
-      return *why = "inflow state needs finite u, rho > 0, theta > 0", LBM_EINVAL;
-  }
-  const bool xp0 = cfg->face[0].kind == LBM_BC_PERIODIC, xp1 = cfg->face[1].kind == LBM_BC_PERIODIC;
-  if (xp0 != xp1) return *why = "a periodic x face must be paired with a periodic x face", LBM_EINVAL;
-  const long long n = static_cast<long long>(cfg->nx) * cfg->ny * cfg->nz;
-  if (n >= (1LL << 31)) return *why = "nx*ny*nz must be < 2^31", LBM_EINVAL;
-
-  const long long elem = static_cast<long long>(lbm::storage_bytes(cfg->storage));
-  g->nx = cfg->nx;
-  g->ny = cfg->ny;
-  g->nz = cfg->nz;
-  g->x_periodic = xp0 ? 1 : 0;
-  if (xp0) {
-    g->xoff = 0;
-    g->pitch = cfg->nx;
-  } else {
-    // Ghost layers; the interior row starts on a 128-byte boundary.
-    const long long align = 128 / elem;
-    g->xoff = static_cast<int>(align);
-    const long long pitch = round_up(align + cfg->nx + rd3q81::kReach, align);
-    if (pitch >= (1LL << 31)) return *why = "row too long", LBM_EINVAL;
-    g->pitch = static_cast<int>(pitch);
-  }
-  g->plane = static_cast<long long>(g->pitch) * cfg->ny;
-  const long long slab = g->plane * cfg->nz;
-  if (slab >= (1LL << 31)) return *why = "one direction slab must hold < 2^31 elements", LBM_EINVAL;
-  g->dir_stride = round_up(slab, 64);
-  g->sub_stride = lbm::kQ * g->dir_stride;
-  return LBM_OK;
-}
 
 size_t buffer_bytes(const lbm::Geometry& g, int storage) {
   return static_cast<size_t>(2 * g.sub_stride) * lbm::storage_bytes(storage);
@@ -168,7 +171,7 @@ lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes) {
   lbm::Geometry g;
   std::string why;
   if (!bytes) return fail(nullptr, LBM_EINVAL, "bytes is NULL");
-  if (plan(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+  if (lbm::plan_geometry(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
   const long long sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
   *bytes = 2 * buffer_bytes(g, cfg->storage) + scratch_bytes(sites) + aux_bytes(g);
   return LBM_OK;
@@ -179,7 +182,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   *out = nullptr;
   lbm::Geometry g;
   std::string why;
-  if (plan(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
+  if (lbm::plan_geometry(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
 
   lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
   if (!ctx) return fail(nullptr, LBM_ENOMEM, "host allocation failed");

@@ -45,36 +45,52 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
   const long long gs = first + k;
   const int sub = gs >= n ? 1 : 0;
   const long long off = site_offset(g, sub, gs - sub * n);
-  double feq[kQ];
-  equilibrium_f64(rho[k], u[k], u[us + k], u[2 * us + k], theta[k], tab, feq);
+  // The equilibrium is evaluated in the arithmetic the step kernel uses for this storage:
+  // FP64 for FP64 populations, FP32 otherwise (offset storage directly as feq/w - 1).
+  using R = typename Codec<S>::Real;
+  R feq[kQ];
+  equilibrium_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab, feq);
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
-    encode<S>(buf + off + i * g.dir_stride, feq[i], tab.w[rd3q81::kDirs[i].shell]);
+    if constexpr (Codec<S>::kOffset)
+      Codec<S>::store(buf + off + i * g.dir_stride, feq[i] - R(1));
+    else
+      Codec<S>::store(buf + off + i * g.dir_stride, feq[i]);
   });
 }
 
-// Moments of the stored populations in FP64 (Eq. (conslaws)); for offset storage as
-// deviations from the weights' own moments (1, 0, 3 theta0).
+// Moments of the stored populations (Eq. (conslaws)), returned in FP64; for offset storage
+// as deviations from the weights' own moments (1, 0, 3 theta0).  FP64 populations are summed
+// in FP64.  FP32/FP16/BF16 values are summed shell by shell in FP32 (at most 12 values of
+// one magnitude class, exact to the storage's own precision), and the 11 shell sums are
+// combined in FP64: FP64-quality moments at a tenth of the FP64 operations.
 template <class S>
 __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTables& tab, const S* buf,
                                              long long off, double& rho, double& jx, double& jy,
                                              double& jz, double& e) {
-  rho = jx = jy = jz = e = 0.0;
+  using R = typename Codec<S>::Real;
+  R sr[kShells], sx[kShells], sy[kShells], sz[kShells];
+#pragma unroll
+  for (int s = 0; s < kShells; ++s) sr[s] = sx[s] = sy[s] = sz[s] = R(0);
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
-    constexpr double c2 = rd3q81::kShellC2[d.shell];
-    const S v = buf[off + i * g.dir_stride];
-    double f;
-    if constexpr (Codec<S>::kOffset)
-      f = tab.w[d.shell] * static_cast<double>(Codec<S>::load(&v));
-    else
-      f = static_cast<double>(v);
-    rho += f;
-    e += c2 * f;
-    if constexpr (d.hx != 0) jx += 0.5 * d.hx * f;
-    if constexpr (d.hy != 0) jy += 0.5 * d.hy * f;
-    if constexpr (d.hz != 0) jz += 0.5 * d.hz * f;
+    const R f = Codec<S>::load(buf + off + i * g.dir_stride);
+    sr[d.shell] += f;
+    if constexpr (d.hx != 0) sx[d.shell] += R(0.5 * d.hx) * f;
+    if constexpr (d.hy != 0) sy[d.shell] += R(0.5 * d.hy) * f;
+    if constexpr (d.hz != 0) sz[d.shell] += R(0.5 * d.hz) * f;
+  });
+  rho = jx = jy = jz = e = 0.0;
+  static_for<kShells>([&](auto Sc) {
+    constexpr int s = decltype(Sc)::value;
+    constexpr double c2 = rd3q81::kShellC2[s];
+    const double ws = Codec<S>::kOffset ? tab.w[s] : 1.0;
+    rho += ws * static_cast<double>(sr[s]);
+    e += ws * c2 * static_cast<double>(sr[s]);
+    jx += ws * static_cast<double>(sx[s]);
+    jy += ws * static_cast<double>(sy[s]);
+    jz += ws * static_cast<double>(sz[s]);
   });
   if constexpr (Codec<S>::kOffset) {
     rho += 1.0;

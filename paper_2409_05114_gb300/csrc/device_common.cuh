@@ -97,24 +97,42 @@ __host__ __device__ __forceinline__ void eq_pair_parts(const EqScalars<R>& e, R&
   od = xi * (a1 + e.a3 * xi2) + e.a4 * psi;
 }
 
-// Full FP64 equilibrium of one state, feq[i] in the library's direction order.
-__host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy, double uz,
-                                                double theta, const LatticeTables& tab, double* feq) {
-  const double eta = theta / tab.theta0 - 1.0;
-  EqScalars<double> e;
-  eq_scalars<double>(ux, uy, uz, theta, eta, tab.na, tab.nb, e);
-  double W[kShells];
-  for (int s = 0; s < kShells; ++s) W[s] = rho * poly4(tab.wp[s], eta);
+// Full equilibrium of one state in arithmetic R (float or double), feq[i] in the library's
+// direction order.  With kOverW it returns feq_i / w_i instead (offset storage).
+template <class R, bool kOverW = false>
+__host__ __device__ inline void equilibrium_all(R rho, R ux, R uy, R uz, R theta, const LatticeTables& tab,
+                                                R* feq) {
+  const bool dbl = sizeof(R) == sizeof(double);
+  const R eta = theta / R(tab.theta0) - R(1);
+  R na[5], nb[5];
+  for (int k = 0; k < 5; ++k) {
+    na[k] = dbl ? R(tab.na[k]) : R(tab.naf[k]);
+    nb[k] = dbl ? R(tab.nb[k]) : R(tab.nbf[k]);
+  }
+  EqScalars<R> e;
+  eq_scalars<R>(ux, uy, uz, theta, eta, na, nb, e);
+  R W[kShells];
+  for (int s = 0; s < kShells; ++s) {
+    R c[5];
+    for (int k = 0; k < 5; ++k)
+      c[k] = kOverW ? (dbl ? R(tab.p[s][k]) : R(tab.pf[s][k])) : (dbl ? R(tab.wp[s][k]) : R(tab.wpf[s][k]));
+    W[s] = rho * poly4(c, eta);
+  }
   // rest particle: xi = psi = 0
-  feq[0] = W[0] * (e.c0 + e.k0 * (0.0 - e.t3));
+  feq[0] = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
   static_for<kPairs>([&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
     constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
-    double ev, od;
-    eq_pair_parts<P, double>(e, ev, od);
+    R ev, od;
+    eq_pair_parts<P, R>(e, ev, od);
     feq[1 + 2 * P] = W[s] * (ev + od);
     feq[2 + 2 * P] = W[s] * (ev - od);
   });
+}
+
+__host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy, double uz,
+                                                double theta, const LatticeTables& tab, double* feq) {
+  equilibrium_all<double, false>(rho, ux, uy, uz, theta, tab, feq);
 }
 
 // Wrap an index displaced by at most kReach into [0, n).

@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
+#include "lbm.h"
 #include "rd3q81.h"
 
 namespace lbm {
@@ -66,6 +68,9 @@ struct StepParams {
   unsigned int* flag;    // set to nonzero when a site sees rho <= 0, theta <= 0 or non-finite
   LatticeTables tab;
 };
+
+// Validates cfg and derives its buffer geometry (api.cu); LBM_OK or LBM_EINVAL with *why.
+lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why);
 
 // Storage codecs.  FP64 / FP32 store f_i itself.  FP16 / BF16 store the offset
 // d_i = f_i / w_i - 1 (f_i = w_i (1 + d_i)); the collide then works on d directly.

@@ -1,0 +1,624 @@
+// Continuous-batching server: many independent RD3Q81 cases resident on one GPU, advanced
+// together by one persistent fused kernel per time step.
+//
+// Each admitted case owns two population buffers (ping-pong) and a slot in a device case
+// table.  A step of the whole batch is (a) one batched zero-gradient ghost fill (only if a
+// resident case has such a face) and (b) one persistent kernel whose blocks walk a packed
+// index of 128-site tiles over all cases: the tile's case is found by binary search over the
+// cases' first-tile offsets, and the site is updated by exactly the same code path as the
+// single-case kernel (site_update), so a case's result is bitwise the same alone and in any
+// mix.  K steps form one "tick", captured once per (membership, K) as a CUDA graph and
+// replayed.  A scheduler thread admits queued requests by HBM footprint on a separate
+// stream while the current tick runs, and retires finished or unstable cases after it.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "lbm.h"
+#include "stream_collide.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kMaxServerCases = 1024;
+constexpr int kTickSteps = 16;            // longest tick (steps between scheduler decisions)
+constexpr long long kXferChunk = 1LL << 21;  // sites per host transfer chunk
+
+struct CaseDesc {
+  Geometry g;
+  void* buf[2];
+  double omega;
+  unsigned int* flag;
+  int storage;         // kF32, kF16Off or kBF16Off
+  int parity;          // buffer holding the state at the start of the tick
+  int tiles_sub;       // ceil(nx*ny*nz / kScBlock)
+  int zg_face[2];      // zero-gradient at -x / +x
+  long long tile0;     // first packed tile
+  long long row0;      // first packed ghost row (zero-gradient faces)
+  long long rows_face; // rows per zero-gradient face: 2 * 81 * nz * ny
+};
+
+__device__ __forceinline__ int find_case(const long long* first, int ncases, long long idx) {
+  int lo = 0, hi = ncases - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class S>
+__device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, int par, const LatticeTables& tab) {
+  if (sub == 0)
+    site_update<S, false, 0>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
+  else
+    site_update<S, false, 1>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
+}
+
+// Step k of the current tick for every resident case.  Grid: persistent (SMs x resident
+// blocks); block b handles tiles b, b + gridDim.x, ...  No block waits on another.
+__global__ void __launch_bounds__(kScBlock) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
+                                                               long long total_tiles, int k, const LatticeTables tab) {
+  __shared__ long long s_first[kMaxServerCases];
+  for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].tile0;
+  __syncthreads();
+  for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    const int c = find_case(s_first, ncases, tile);
+    const CaseDesc& cd = cases[c];
+    const long long local = tile - cd.tile0;
+    const int sub = local >= cd.tiles_sub ? 1 : 0;
+    const long long t = (local - static_cast<long long>(sub) * cd.tiles_sub) * kScBlock + threadIdx.x;
+    const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
+    if (t >= n) continue;
+    const int par = (cd.parity + k) & 1;
+    switch (cd.storage) {
+      case kF32: served_site<float>(cd, sub, static_cast<int>(t), par, tab); break;
+      case kF16Off: served_site<__half>(cd, sub, static_cast<int>(t), par, tab); break;
+      default: served_site<__nv_bfloat16>(cd, sub, static_cast<int>(t), par, tab); break;
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void copy_edge(T* buf, const CaseDesc& cd, long long row, int face) {
+  const Geometry& g = cd.g;
+  if (face == 0) {
+    const T v = buf[row + g.xoff];
+    for (int l = 1; l <= rd3q81::kReach; ++l) buf[row + g.xoff - l] = v;
+  } else {
+    const T v = buf[row + g.xoff + g.nx - 1];
+    for (int l = 0; l < rd3q81::kReach; ++l) buf[row + g.xoff + g.nx + l] = v;
+  }
+}
+
+// Zero-gradient ghost fill of step k for all resident cases: thread per (case, face, sub,
+// i, z, y) row; raw copies of the stored values (no decode needed).
+__global__ void served_zero_gradient_kernel(const CaseDesc* __restrict__ cases, int ncases, long long total_rows,
+                                            int k) {
+  __shared__ long long s_first[kMaxServerCases];
+  for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].row0;
+  __syncthreads();
+  for (long long r = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; r < total_rows;
+       r += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = find_case(s_first, ncases, r);
+    const CaseDesc& cd = cases[c];
+    long long local = r - cd.row0;
+    int which = static_cast<int>(local / cd.rows_face);  // index among this case's zg faces
+    local -= which * cd.rows_face;
+    const int face = (cd.zg_face[0] && which == 0) ? 0 : 1;
+    const Geometry& g = cd.g;
+    const int y = static_cast<int>(local % g.ny);
+    const long long q = local / g.ny;
+    const int z = static_cast<int>(q % g.nz);
+    const long long si = q / g.nz;
+    const long long row = (si / kQ) * g.sub_stride + (si % kQ) * g.dir_stride + z * g.plane +
+                          static_cast<long long>(y) * g.pitch;
+    void* b = cd.buf[(cd.parity + k) & 1];
+    if (cd.storage == kF32)
+      copy_edge(static_cast<uint32_t*>(b), cd, row, face);
+    else
+      copy_edge(static_cast<uint16_t*>(b), cd, row, face);
+  }
+}
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  long long ticket = 0;
+  lbm_config cfg{};
+  long long nsteps = 0;
+  long long sites = 0;
+  size_t footprint = 0;
+  std::vector<double> in;   // rho | u (3 * sites) | theta
+  std::vector<double> out;  // same layout, filled at retirement
+  Clock::time_point t_submit, t_done;
+  lbm_status status = LBM_EBUSY;
+  bool done = false;
+};
+
+struct Resident {
+  std::shared_ptr<Request> req;
+  Geometry g{};
+  void* buf[2] = {nullptr, nullptr};
+  int slot = -1;
+  int parity = 0;
+  long long steps_left = 0;
+  double omega = 0.0;
+  bool zg[2] = {false, false};
+  cudaEvent_t ready = nullptr;  // admission finished (on the admission stream)
+};
+
+}  // namespace
+}  // namespace lbm
+
+struct lbm_server {
+  using Request = lbm::Request;
+  using Resident = lbm::Resident;
+
+  size_t budget = 0;
+  int max_cases = 0;
+  int device = 0;
+  lbm::LatticeTables tab{};
+  cudaStream_t compute = nullptr, admit = nullptr;
+  lbm::CaseDesc* d_cases = nullptr;
+  lbm::CaseDesc* h_cases = nullptr;  // pinned staging
+  unsigned int* d_flags = nullptr;
+  unsigned int* h_flags = nullptr;   // pinned
+  double* d_admit_scratch = nullptr;
+  double* d_retire_scratch = nullptr;
+  int grid_blocks = 0;
+
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;          // submitted, not admitted
+  std::unordered_map<long long, std::shared_ptr<Request>> requests;
+  std::vector<Resident> active, joining;
+  std::vector<int> free_slots;
+  size_t resident_bytes = 0;
+  long long next_ticket = 1;
+  bool stop = false;
+  lbm_status fatal = LBM_OK;
+  std::string err = "no error";
+  lbm_server_stats stats{};
+  lbm::Clock::time_point busy_since;
+
+  // graphs per (version, K)
+  long long version = 0;
+  std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
+  std::thread worker;
+};
+
+namespace lbm {
+namespace {
+
+thread_local std::string g_server_error = "no error";
+
+lbm_status set_fatal(lbm_server* s, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->fatal = LBM_ECUDA;
+  s->err = msg;
+  s->cv_done.notify_all();
+  return LBM_ECUDA;
+}
+
+#define SRV_CK(s, call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return set_fatal(s, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Starts the admission of request r into a free slot (asynchronous, on the admission stream).
+lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int slot) {
+  Resident res;
+  res.req = r;
+  res.slot = slot;
+  res.steps_left = r->nsteps;
+  res.omega = 2.0 / (2.0 * r->cfg.tau + 1.0);
+  std::string why;
+  plan_geometry(&r->cfg, &res.g, &why);
+  res.zg[0] = r->cfg.face[0].kind == LBM_BC_ZERO_GRADIENT;
+  res.zg[1] = r->cfg.face[1].kind == LBM_BC_ZERO_GRADIENT;
+  const size_t bb = static_cast<size_t>(2 * res.g.sub_stride) * storage_bytes(r->cfg.storage);
+  for (int b = 0; b < 2; ++b) SRV_CK(s, cudaMallocAsync(&res.buf[b], bb, s->admit));
+  SRV_CK(s, cudaMemsetAsync(s->d_flags + slot, 0, sizeof(unsigned int), s->admit));
+  const long long S = r->sites;
+  double* sr = s->d_admit_scratch;
+  double* su = sr + kXferChunk;
+  double* st = su + 3 * kXferChunk;
+  for (long long first = 0; first < S; first += kXferChunk) {
+    const long long cnt = std::min(kXferChunk, S - first);
+    const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
+    SRV_CK(s, cudaMemcpyAsync(sr, r->in.data() + first, nb, cudaMemcpyHostToDevice, s->admit));
+    for (int a = 0; a < 3; ++a)
+      SRV_CK(s, cudaMemcpyAsync(su + a * cnt, r->in.data() + S + a * S + first, nb, cudaMemcpyHostToDevice, s->admit));
+    SRV_CK(s, cudaMemcpyAsync(st, r->in.data() + 4 * S + first, nb, cudaMemcpyHostToDevice, s->admit));
+    SRV_CK(s, launch_init(r->cfg.storage, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt, s->admit));
+    ++s->stats.kernel_launches;
+  }
+  for (int face = 0; face < 2; ++face) {
+    const lbm_bc& b = r->cfg.face[face];
+    if (b.kind != LBM_BC_EQ_INFLOW) continue;
+    Feq81 feq;
+    equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, s->tab, feq.v);
+    for (int k = 0; k < 2; ++k) {
+      SRV_CK(s, launch_fill_inflow(r->cfg.storage, res.g, s->tab, res.buf[k], face, feq, s->admit));
+      ++s->stats.kernel_launches;
+    }
+  }
+  SRV_CK(s, cudaEventCreateWithFlags(&res.ready, cudaEventDisableTiming));
+  SRV_CK(s, cudaEventRecord(res.ready, s->admit));
+  // the admission stream reuses its scratch only after this case's copies are done
+  SRV_CK(s, cudaStreamSynchronize(s->admit));
+  s->joining.push_back(res);
+  return LBM_OK;
+}
+
+// Admits queued requests in FIFO order while a slot and budget are free.
+lbm_status admit_some(lbm_server* s) {
+  for (;;) {
+    std::shared_ptr<Request> r;
+    int slot = -1;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->queue.empty() || s->free_slots.empty()) return LBM_OK;
+      if (s->resident_bytes + s->queue.front()->footprint > s->budget) return LBM_OK;
+      r = s->queue.front();
+      s->queue.pop_front();
+      slot = s->free_slots.back();
+      s->free_slots.pop_back();
+      s->resident_bytes += r->footprint;
+      s->stats.peak_resident_bytes = std::max(s->stats.peak_resident_bytes, s->resident_bytes);
+      ++s->stats.admitted;
+    }
+    lbm_status st = start_admission(s, r, slot);
+    if (st != LBM_OK) return st;
+  }
+}
+
+cudaGraphExec_t tick_graph(lbm_server* s, int ncases, long long total_tiles, long long total_rows, int K) {
+  auto key = std::make_pair(s->version, K);
+  auto it = s->graphs.find(key);
+  if (it != s->graphs.end()) return it->second;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, std::max<long long>(total_tiles, 1)));
+  for (int k = 0; ok && k < K; ++k) {
+    if (total_rows > 0) {
+      const int zb = static_cast<int>(std::min<long long>((total_rows + 255) / 256, 4096));
+      served_zero_gradient_kernel<<<zb, 256, 0, cap>>>(s->d_cases, ncases, total_rows, k);
+    }
+    served_step_kernel<<<grid, kScBlock, 0, cap>>>(s->d_cases, ncases, total_tiles, k, s->tab);
+  }
+  if (ok) ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
+  if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (!ok) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  s->graphs[key] = exec;
+  return exec;
+}
+
+void drop_graphs(lbm_server* s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
+}
+
+// Copies a retiring case's fields to its request and releases its memory.
+lbm_status retire(lbm_server* s, Resident& res, lbm_status status) {
+  Request& r = *res.req;
+  const long long S = r.sites;
+  r.out.assign(static_cast<size_t>(5 * S), 0.0);
+  double* sr = s->d_retire_scratch;
+  double* su = sr + kXferChunk;
+  double* st = su + 3 * kXferChunk;
+  for (long long first = 0; first < S; first += kXferChunk) {
+    const long long cnt = std::min(kXferChunk, S - first);
+    const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
+    SRV_CK(s, launch_moments(r.cfg.storage, res.g, s->tab, res.buf[res.parity], sr, su, st, first, cnt, cnt,
+                             s->compute));
+    ++s->stats.kernel_launches;
+    SRV_CK(s, cudaMemcpyAsync(r.out.data() + first, sr, nb, cudaMemcpyDeviceToHost, s->compute));
+    for (int a = 0; a < 3; ++a)
+      SRV_CK(s, cudaMemcpyAsync(r.out.data() + S + a * S + first, su + a * cnt, nb, cudaMemcpyDeviceToHost,
+                                s->compute));
+    SRV_CK(s, cudaMemcpyAsync(r.out.data() + 4 * S + first, st, nb, cudaMemcpyDeviceToHost, s->compute));
+  }
+  for (int b = 0; b < 2; ++b) SRV_CK(s, cudaFreeAsync(res.buf[b], s->compute));
+  SRV_CK(s, cudaStreamSynchronize(s->compute));
+  if (res.ready) cudaEventDestroy(res.ready);
+  std::lock_guard<std::mutex> lk(s->mu);
+  r.t_done = Clock::now();
+  r.status = status;
+  r.done = true;
+  r.in.clear();
+  r.in.shrink_to_fit();
+  s->resident_bytes -= r.footprint;
+  s->free_slots.push_back(res.slot);
+  ++s->stats.completed;
+  if (status == LBM_EUNSTABLE) ++s->stats.unstable;
+  else s->stats.site_updates += S * r.nsteps;
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+  return LBM_OK;
+}
+
+lbm_status run_tick(lbm_server* s) {
+  // join cases whose admission finished
+  if (!s->joining.empty()) {
+    for (auto& j : s->joining) {
+      SRV_CK(s, cudaStreamWaitEvent(s->compute, j.ready, 0));
+      s->active.push_back(j);
+    }
+    s->joining.clear();
+    ++s->version;
+    drop_graphs(s);
+  }
+  if (s->active.empty()) return LBM_OK;
+  const int ncases = static_cast<int>(s->active.size());
+  long long total_tiles = 0, total_rows = 0, min_left = s->active[0].steps_left;
+  for (int c = 0; c < ncases; ++c) {
+    Resident& a = s->active[c];
+    CaseDesc& d = s->h_cases[c];
+    d.g = a.g;
+    d.buf[0] = a.buf[0];
+    d.buf[1] = a.buf[1];
+    d.omega = a.omega;
+    d.flag = s->d_flags + a.slot;
+    d.storage = a.req->cfg.storage;
+    d.parity = a.parity;
+    const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
+    d.tiles_sub = static_cast<int>((n + kScBlock - 1) / kScBlock);
+    d.tile0 = total_tiles;
+    total_tiles += 2LL * d.tiles_sub;
+    d.zg_face[0] = a.zg[0];
+    d.zg_face[1] = a.zg[1];
+    d.rows_face = 2LL * kQ * a.g.nz * a.g.ny;
+    d.row0 = total_rows;
+    total_rows += (a.zg[0] + a.zg[1]) * d.rows_face;
+    min_left = std::min(min_left, a.steps_left);
+  }
+  const int K = static_cast<int>(std::min<long long>(kTickSteps, min_left));
+  SRV_CK(s, cudaMemcpyAsync(s->d_cases, s->h_cases, sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, s->compute));
+  cudaGraphExec_t g = tick_graph(s, ncases, total_tiles, total_rows, K);
+  if (!g) return set_fatal(s, "CUDA graph capture of a serving tick failed");
+  SRV_CK(s, cudaGraphLaunch(g, s->compute));
+  ++s->stats.graph_launches;
+  s->stats.kernel_launches += static_cast<long long>(K) * (total_rows > 0 ? 2 : 1);
+  ++s->stats.ticks;
+  SRV_CK(s, cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(unsigned int) * s->max_cases, cudaMemcpyDeviceToHost,
+                            s->compute));
+  // overlap: admit newly arrived requests while the tick runs
+  lbm_status st = admit_some(s);
+  if (st != LBM_OK) return st;
+  SRV_CK(s, cudaStreamSynchronize(s->compute));
+  std::vector<Resident> keep;
+  for (auto& a : s->active) {
+    a.steps_left -= K;
+    a.parity ^= (K & 1);
+    const bool unstable = s->h_flags[a.slot] != 0;
+    if (a.steps_left == 0 || unstable) {
+      st = retire(s, a, unstable ? LBM_EUNSTABLE : LBM_OK);
+      if (st != LBM_OK) return st;
+    } else {
+      keep.push_back(a);
+    }
+  }
+  if (keep.size() != s->active.size()) {
+    ++s->version;
+    drop_graphs(s);
+  }
+  s->active.swap(keep);
+  return LBM_OK;
+}
+
+void worker_main(lbm_server* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop || s->fatal != LBM_OK) break;
+      if (s->active.empty() && s->joining.empty() && s->queue.empty())
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+      if (s->stop) break;
+    }
+    if (admit_some(s) != LBM_OK) break;
+    if (s->active.empty() && s->joining.empty()) continue;
+    const auto t0 = Clock::now();
+    if (run_tick(s) != LBM_OK) break;
+    const auto t1 = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stats.busy_seconds += std::chrono::duration<double>(t1 - t0).count();
+    s->stats.resident_cases = static_cast<int>(s->active.size());
+  }
+}
+
+}  // namespace
+}  // namespace lbm
+
+extern "C" {
+
+lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server** out) {
+  using namespace lbm;
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (hbm_budget_bytes == 0 || max_cases < 1 || max_cases > kMaxServerCases) {
+    g_server_error = "need hbm_budget_bytes > 0 and 1 <= max_cases <= 1024";
+    return LBM_EINVAL;
+  }
+  auto* s = new (std::nothrow) lbm_server();
+  if (!s) return LBM_ENOMEM;
+  s->budget = hbm_budget_bytes;
+  s->max_cases = max_cases;
+  build_lattice_tables(&s->tab);
+  for (int i = max_cases - 1; i >= 0; --i) s->free_slots.push_back(i);
+  auto bail = [&](const std::string& msg) {
+    g_server_error = msg;
+    lbm_server_destroy(s);
+    return LBM_ECUDA;
+  };
+  if (cudaGetDevice(&s->device) != cudaSuccess) return bail("cudaGetDevice failed");
+  if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess)
+    return bail("stream creation failed");
+  if (cudaMalloc(&s->d_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
+      cudaMallocHost(&s->h_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
+      cudaMalloc(&s->d_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
+      cudaMallocHost(&s->h_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
+      cudaMalloc(&s->d_admit_scratch, 5 * kXferChunk * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&s->d_retire_scratch, 5 * kXferChunk * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail("device allocation failed");
+  }
+  cudaMemset(s->d_flags, 0, sizeof(unsigned int) * max_cases);
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel, kScBlock, 0);
+  s->grid_blocks = std::max(1, sms * std::max(1, per_sm));
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return LBM_OK;
+}
+
+lbm_status lbm_submit(lbm_server* s, const lbm_config* cfg, const double* rho, const double* u, const double* theta,
+                      long long nsteps, long long* ticket) {
+  using namespace lbm;
+  if (!s || !cfg || !rho || !u || !theta || !ticket || nsteps < 1) return LBM_EINVAL;
+  Geometry g;
+  std::string why;
+  if (plan_geometry(cfg, &g, &why) != LBM_OK) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = why;
+    return LBM_EINVAL;
+  }
+  if (cfg->storage == LBM_F64 || cfg->fp64_moments) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments";
+    return LBM_EINVAL;
+  }
+  auto r = std::make_shared<Request>();
+  r->cfg = *cfg;
+  r->nsteps = nsteps;
+  r->sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
+  r->footprint = static_cast<size_t>(2 * 2 * g.sub_stride) * storage_bytes(cfg->storage);
+  if (r->footprint > s->budget) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "case footprint exceeds the server's HBM budget";
+    ++s->stats.rejected;
+    return LBM_ENOMEM;
+  }
+  const long long S = r->sites;
+  r->in.resize(static_cast<size_t>(5 * S));
+  std::memcpy(r->in.data(), rho, S * sizeof(double));
+  std::memcpy(r->in.data() + S, u, 3 * S * sizeof(double));
+  std::memcpy(r->in.data() + 4 * S, theta, S * sizeof(double));
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->fatal != LBM_OK) return s->fatal;
+    r->ticket = s->next_ticket++;
+    s->queue.push_back(r);
+    s->requests[r->ticket] = r;
+    ++s->stats.submitted;
+  }
+  s->cv_work.notify_all();
+  *ticket = r->ticket;
+  return LBM_OK;
+}
+
+lbm_status lbm_poll(lbm_server* s, long long ticket, double* rho, double* u, double* theta, double* latency_s) {
+  using namespace lbm;
+  if (!s) return LBM_EINVAL;
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->requests.find(ticket);
+    if (it == s->requests.end()) return LBM_ENOTFOUND;
+    r = it->second;
+    if (!r->done) return s->fatal != LBM_OK ? s->fatal : LBM_EBUSY;
+    s->requests.erase(it);
+  }
+  const long long S = r->sites;
+  if (rho) std::memcpy(rho, r->out.data(), S * sizeof(double));
+  if (u) std::memcpy(u, r->out.data() + S, 3 * S * sizeof(double));
+  if (theta) std::memcpy(theta, r->out.data() + 4 * S, S * sizeof(double));
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  return r->status;
+}
+
+lbm_status lbm_wait(lbm_server* s, long long ticket, double timeout_s) {
+  using namespace lbm;
+  if (!s || !(timeout_s >= 0)) return LBM_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->requests.find(ticket);
+  if (it == s->requests.end()) return LBM_ENOTFOUND;
+  auto r = it->second;
+  const bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                      [&] { return r->done || s->fatal != LBM_OK; });
+  if (s->fatal != LBM_OK) return s->fatal;
+  return ok ? LBM_OK : LBM_ETIMEOUT;
+}
+
+lbm_status lbm_server_get_stats(lbm_server* s, lbm_server_stats* out) {
+  if (!s || !out) return LBM_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->resident_bytes = s->resident_bytes;
+  out->queued = static_cast<long long>(s->queue.size());
+  return LBM_OK;
+}
+
+const char* lbm_server_last_error(const lbm_server* s) {
+  if (!s) return lbm::g_server_error.c_str();
+  return s->err.c_str();
+}
+
+lbm_status lbm_server_destroy(lbm_server* s) {
+  using namespace lbm;
+  if (!s) return LBM_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
+  if (s->compute) cudaStreamSynchronize(s->compute);
+  if (s->admit) cudaStreamSynchronize(s->admit);
+  for (auto* v : {&s->active, &s->joining})
+    for (auto& a : *v) {
+      for (int b = 0; b < 2; ++b)
+        if (a.buf[b]) cudaFree(a.buf[b]);
+      if (a.ready) cudaEventDestroy(a.ready);
+    }
+  drop_graphs(s);
+  if (s->d_cases) cudaFree(s->d_cases);
+  if (s->h_cases) cudaFreeHost(s->h_cases);
+  if (s->d_flags) cudaFree(s->d_flags);
+  if (s->h_flags) cudaFreeHost(s->h_flags);
+  if (s->d_admit_scratch) cudaFree(s->d_admit_scratch);
+  if (s->d_retire_scratch) cudaFree(s->d_retire_scratch);
+  if (s->compute) cudaStreamDestroy(s->compute);
+  if (s->admit) cudaStreamDestroy(s->admit);
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  delete s;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -42,13 +42,15 @@ __device__ __forceinline__ const R* tab_nb(const LatticeTables& t) {
   if constexpr (std::is_same_v<R, double>) return t.nb; else return t.nbf;
 }
 
+// Updates interior site t of sublattice SUB: reads `src`, writes `dst` (both whole
+// population buffers of geometry g), relaxation omega, instability flag `flag`.
 // kF64Mom: the moment sums and the temperature recovery run in FP64 whatever the storage.
 template <class Store, bool kF64Mom, int SUB>
-__device__ __forceinline__ void site_update(const StepParams& p, int t) {
+__device__ __forceinline__ void site_update(const Geometry& g, const void* src_buf, void* dst_buf, double omega,
+                                            unsigned int* flag, const LatticeTables& tb, int t) {
   using C = Codec<Store>;
   using R = typename C::Real;                                  // collide arithmetic
   using M = std::conditional_t<kF64Mom, double, R>;            // moment arithmetic
-  const Geometry& g = p.g;
 
   const int x = t % g.nx;
   const int r = t / g.nx;
@@ -66,7 +68,7 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
   }
 
   // ---- pull -----------------------------------------------------------------------------
-  const Store* src = static_cast<const Store*>(p.src);
+  const Store* src = static_cast<const Store*>(src_buf);
   const Store* same = src + SUB * g.sub_stride;
   const Store* other = src + (1 - SUB) * g.sub_stride;
   R f[kQ];
@@ -84,9 +86,13 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
   // ---- moments, Eq. (conslaws) ----------------------------------------------------------
   // Offset storage holds d_i = f_i/w_i - 1, so rho = 1 + <w, d>, j = <w, d c>,
   // <f, c^2> = 3 theta0 + <w, d c^2> (the weights' own moments are 1, 0, 3 theta0).
-  const LatticeTables& tb = p.tab;
+  // FP32 sums of FP32 populations are also taken over the deviations f_i - w_i: the same
+  // moments, summed from numbers ~10x smaller than f_i, hence ~10x smaller rounding.
+  constexpr bool kDev = C::kOffset || std::is_same_v<M, float>;
   M rho, jx = M(0), jy = M(0), jz = M(0), E = M(0);
-  if constexpr (C::kOffset) rho = tab_w<M>(tb, 0) * M(f[0]); else rho = M(f[0]);
+  if constexpr (C::kOffset) rho = tab_w<M>(tb, 0) * M(f[0]);
+  else if constexpr (kDev) rho = M(f[0]) - tab_w<M>(tb, 0);
+  else rho = M(f[0]);
   static_for<kPairs>([&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
@@ -99,6 +105,8 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
       const M ws = tab_w<M>(tb, d.shell);
       sum *= ws;
       dif *= ws;
+    } else if constexpr (kDev) {
+      sum -= M(2) * tab_w<M>(tb, d.shell);
     }
     rho += sum;
     E += M(c2) * sum;
@@ -106,7 +114,7 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
     if constexpr (d.hy != 0) jy += M(0.5 * d.hy) * dif;
     if constexpr (d.hz != 0) jz += M(0.5 * d.hz) * dif;
   });
-  if constexpr (C::kOffset) {
+  if constexpr (kDev) {
     rho += M(1);
     E += M(3.0 * rd3q81::kTheta0);
   }
@@ -116,7 +124,7 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
 
   const R rh = R(rho);
   const R theta = R(mtheta);
-  if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(p.flag, 1u);
+  if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(flag, 1u);
 
   // ---- equilibrium scalars, App. B ------------------------------------------------------
   const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
@@ -129,15 +137,28 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
     W[s] = rh * poly4(C::kOffset ? tab_p<R>(tb, s) : tab_wp<R>(tb, s), eta);
 
   // ---- BGK collision, Eq. (discretelbm) -------------------------------------------------
-  const R om = R(p.omega);
+  // f_i <- f_i + omega D_i with D_i = f~eq_i - f_i.  In exact arithmetic D has zero mass,
+  // momentum and energy.  In FP32 it does not quite (f~eq is evaluated at rho, u, theta
+  // rounded to FP32), and the defect would accumulate step after step.  For FP32 storage
+  // the defects of D are therefore summed (D is small, so the sums are accurate) and removed
+  // by subtracting w_i (a + b.c_i + g c_i^2) with a, b, g fixed by the weights' moments
+  // <w,1> = 1, <w,c c> = theta0 I, <w,c^2> = 3 theta0, <w,c^4> = 15 theta0^2.  The result
+  // equals the plain update in exact arithmetic; in FP32 it conserves to the sums' rounding.
+  constexpr bool kProject = std::is_same_v<Store, float>;
+  const R om = R(omega);
+  R d1 = R(0), dE = R(0), dx = R(0), dy = R(0), dz = R(0);
   {
     R feq0 = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
     if constexpr (C::kOffset) feq0 -= R(1);
-    f[0] += om * (feq0 - f[0]);
+    const R D0 = feq0 - f[0];
+    if constexpr (kProject) d1 = D0;
+    f[0] += om * D0;
   }
   static_for<kPairs>([&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
-    constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+    constexpr int s = d.shell;
+    constexpr double c2 = rd3q81::kShellC2[s];
     R ev, od;
     eq_pair_parts<P, R>(e, ev, od);
     const R we = W[s] * ev;
@@ -147,12 +168,44 @@ __device__ __forceinline__ void site_update(const StepParams& p, int t) {
       fp -= R(1);
       fm -= R(1);
     }
-    f[1 + 2 * P] += om * (fp - f[1 + 2 * P]);
-    f[2 + 2 * P] += om * (fm - f[2 + 2 * P]);
+    const R Dp = fp - f[1 + 2 * P];
+    const R Dm = fm - f[2 + 2 * P];
+    if constexpr (kProject) {
+      const R sD = Dp + Dm, dD = Dp - Dm;
+      d1 += sD;
+      dE += R(c2) * sD;
+      if constexpr (d.hx != 0) dx += R(0.5 * d.hx) * dD;
+      if constexpr (d.hy != 0) dy += R(0.5 * d.hy) * dD;
+      if constexpr (d.hz != 0) dz += R(0.5 * d.hz) * dD;
+    }
+    f[1 + 2 * P] += om * Dp;
+    f[2 + 2 * P] += om * Dm;
   });
+  if constexpr (kProject) {
+    constexpr double t0 = rd3q81::kTheta0;
+    const R g = (dE - R(3.0 * t0) * d1) * R(1.0 / (6.0 * t0 * t0));
+    const R a = d1 - R(3.0 * t0) * g;
+    const R oa = om * a, og = om * g, obx = om * dx * R(1.0 / t0), oby = om * dy * R(1.0 / t0),
+            obz = om * dz * R(1.0 / t0);
+    f[0] -= tab_w<R>(tb, 0) * oa;
+    static_for<kPairs>([&](auto Pc) {
+      constexpr int P = decltype(Pc)::value;
+      constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+      constexpr double c2 = rd3q81::kShellC2[d.shell];
+      const R ws = tab_w<R>(tb, d.shell);
+      const R ce = ws * (oa + R(c2) * og);
+      R co = R(0);
+      if constexpr (d.hx != 0) co += R(0.5 * d.hx) * obx;
+      if constexpr (d.hy != 0) co += R(0.5 * d.hy) * oby;
+      if constexpr (d.hz != 0) co += R(0.5 * d.hz) * obz;
+      co *= ws;
+      f[1 + 2 * P] -= ce + co;
+      f[2 + 2 * P] -= ce - co;
+    });
+  }
 
   // ---- store (coalesced, same site index in the other buffer) ----------------------------
-  Store* dst = static_cast<Store*>(p.dst) + SUB * g.sub_stride + (zs[4] + ys[4] + xs[4]);
+  Store* dst = static_cast<Store*>(dst_buf) + SUB * g.sub_stride + (zs[4] + ys[4] + xs[4]);
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     C::store(dst + static_cast<long long>(i) * g.dir_stride, f[i]);
@@ -165,9 +218,9 @@ __global__ void __launch_bounds__(kScBlock) stream_collide_kernel(const StepPara
   const long long t = static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
   if (t >= n) return;
   if (blockIdx.y == 0)
-    site_update<Store, kF64Mom, 0>(p, static_cast<int>(t));
+    site_update<Store, kF64Mom, 0>(p.g, p.src, p.dst, p.omega, p.flag, p.tab, static_cast<int>(t));
   else
-    site_update<Store, kF64Mom, 1>(p, static_cast<int>(t));
+    site_update<Store, kF64Mom, 1>(p.g, p.src, p.dst, p.omega, p.flag, p.tab, static_cast<int>(t));
 }
 
 template <class Store, bool kF64Mom>

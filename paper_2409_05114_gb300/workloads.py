@@ -137,15 +137,15 @@ def hit(n: int = 256, mach_rms: float = 0.5, seed: int = 2409, tau_lb: float = 0
 
 def mach2_blob(nx: int = 1024, ny: int = 256, nz: int = 4, seed: int = 5114, tau_lb: float = 0.55,
                steps: int = 2000, blob_amp: float = 0.2, sigma: float = 16.0, vortex: float = 0.3,
-               radius: float = 16.0) -> Workload:
-    """Uniform Mach-2 flow in x (U = 2 c_s, rho = 1, theta = theta0), a Gaussian density blob
+               radius: float = 16.0, mach: float = 2.0) -> Workload:
+    """Uniform Mach-2 flow in x (U = mach c_s, mach = 2; rho = 1, theta = theta0), a Gaussian density blob
     (amplitude 0.2, sigma 16 cells, centre drawn from the seed near (nx/4, ny/2)) and an
     isentropic vortex at (nx/4, ny/2): u_phi = eps U (r/R) exp((1 - r^2/R^2)/2),
     theta = theta0 - (2/5) (eps U)^2 / 2 exp(1 - r^2/R^2), rho ~ (theta/theta0)^(3/2).
     Equilibrium inflow of the free stream at -x, zero-gradient outflow at +x."""
     rng = np.random.default_rng(seed)
     x, y, _ = positions(nx, ny, nz)
-    U = 2.0 * CS
+    U = mach * CS
     xc, yc = nx / 4.0, ny / 2.0
     bx, by = xc + rng.uniform(-8, 8), yc + rng.uniform(-8, 8)
     dx, dy = x - xc, y - yc
@@ -158,7 +158,8 @@ def mach2_blob(nx: int = 1024, ny: int = 256, nz: int = 4, seed: int = 5114, tau
     rho = (theta / THETA0) ** 1.5 * blob
     u = np.stack([ux, uy, np.zeros_like(ux)])
     faces = [("eq_inflow", 1.0, U, 0.0, 0.0, THETA0), "zero_gradient"] + ["periodic"] * 4
-    return Workload(f"mach2_blob_{nx}x{ny}x{nz}", nx, ny, nz, tau_lb, steps, rho, u, theta, faces)
+    name = f"mach2_blob_{nx}x{ny}x{nz}" if mach == 2.0 else f"blob_mach{mach:g}_{nx}x{ny}x{nz}"
+    return Workload(name, nx, ny, nz, tau_lb, steps, rho, u, theta, faces)
 
 
 def smooth_random(nx: int, ny: int, nz: int, seed: int = 0, mach: float = 0.3, eta: float = 0.05,

@@ -51,7 +51,12 @@ def _compare_fp64(wl, steps, tau, perm, wlib, populations=None, tol=1e-12):
     return pe, er
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-15), ("f32", 1e-7), ("f16", 2e-3), ("bf16", 1.6e-2)])
+# FP64: the library evaluates the weight polynomials of Table "tab:weights" in FP64 (terms
+# ~1e6 cancelling to ~1e4), so its weights carry ~1e-14 relative error against the oracle's
+# exact rational ones.  FP32: f~eq evaluated in FP32 (the step kernel's arithmetic); the
+# cubic xi-polynomial of the outer shells (|xi|/theta up to ~3) loses a few ulps.
+# FP16/BF16: one rounding of d = f/w - 1.
+@pytest.mark.parametrize("storage,tol", [("f64", 5e-14), ("f32", 3e-6), ("f16", 2e-3), ("bf16", 1.6e-2)])
 def test_init_is_oracle_equilibrium(B, perm, wlib, storage, tol):
     wl = W.smooth_random(13, 6, 5, seed=1, mach=0.5, eta=0.1)
     f_ref = O.init(wl.rho, wl.u, wl.theta)[:, perm]
@@ -83,12 +88,43 @@ def test_fp64_sod_zero_gradient(B, perm, wlib):
 
 
 def test_fp64_inflow_outflow(B, perm, wlib):
-    wl = W.mach2_blob(nx=96, ny=24, nz=4)
+    # Mach-1 blob with vortex: equilibrium inflow at -x, zero-gradient outflow at +x
+    wl = W.mach2_blob(nx=96, ny=24, nz=4, mach=1.0)
     _compare_fp64(wl, 4, wl.paper_tau("literal"), perm, wlib)
     # subsonic inflow on +x, zero-gradient on -x (the other orientation)
     wl2 = W.smooth_random(40, 6, 4, seed=6, mach=0.3, eta=0.05,
                           faces=["zero_gradient", ("eq_inflow", 1.05, -0.2, 0.05, 0.0, W.THETA0 * 1.02)])
     _compare_fp64(wl2, 6, 0.1, perm, wlib)
+
+
+def test_fp64_mach2_blob_first_step(B, perm, wlib):
+    """The Mach-2 blob workload itself: after one step some sites already have theta < 0 in
+    both codes (outside the series equilibrium's range); parity holds while values are
+    finite, and both report the state as unstable."""
+    wl = W.mach2_blob(nx=128, ny=32, nz=4)
+    tau = wl.paper_tau("lb")
+    f_ref = oracle_run(wl, 1, tau)
+    assert np.all(np.isfinite(f_ref))
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, "f64", wl.faces)
+    ctx = B.lbm_create(cfg)
+    try:
+        B.lbm_init(ctx, wl.rho.reshape(-1).copy(), wl.u.reshape(-1).copy(), wl.theta.reshape(-1).copy())
+        B.lbm_step(ctx, 1)
+        f = np.zeros(2 * 81 * wl.nx * wl.ny * wl.nz)
+        B.lbm_get_populations(ctx, f)
+        unstable = False
+        try:
+            B.lbm_sync(ctx)
+        except B.LbmUnstable:
+            unstable = True
+    finally:
+        B.lbm_destroy(ctx)
+    ref = f_ref[:, perm]
+    # Where theta is near 0 the equilibrium (1/theta^3 terms) amplifies rounding: compare
+    # element-wise relative to each value.
+    np.testing.assert_allclose(f.reshape(ref.shape), ref, rtol=1e-9, atol=1e-13)
+    _, _, th = O.fields(f_ref)
+    assert unstable == bool((th <= 0).any())
 
 
 def test_fp64_taylor_green(B, perm, wlib):
@@ -238,11 +274,13 @@ def _sampled_full_size(B, perm, wlib, wl, storage, tol, nsamples=96):
     assert err <= tol, err
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 1e-6)])
+# FP32 per-population bound for one step from FP32 inputs: the FP32 evaluation of the
+# cubic xi-polynomial of the outer shells (emulated bound 1.3e-5), times 3.
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-13), ("f32", 4e-5)])
 def test_full_size_tgv128_sampled(B, perm, wlib, storage, tol):
     _sampled_full_size(B, perm, wlib, W.taylor_green(128), storage, tol)
 
 
 def test_full_size_tgv512_fp32_sampled(B, perm, wlib):
     """The roofline point of the benchmark: 512^3 TGV, FP32 storage (2 x 87 GB)."""
-    _sampled_full_size(B, perm, wlib, W.taylor_green(512), "f32", 1e-6, nsamples=64)
+    _sampled_full_size(B, perm, wlib, W.taylor_green(512), "f32", 4e-5, nsamples=64)
