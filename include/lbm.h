@@ -155,6 +155,23 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * Table "tab:weights").  Either pointer may be NULL.  Returns 81. */
 int lbm_velocities(int* h, double* w);
 
+/* The global sums of lbm_totals (rho, rho u_x, rho u_y, rho u_z, <f, c^2>) for a caller that
+ * cannot allocate device memory -- for example because its own memory pool already holds
+ * the device's free memory, or because it must not call cudaMalloc/cudaFree, which can
+ * synchronise the whole device.  The paper has no counterpart; this is plumbing.  It needs
+ * no context and allocates nothing.  f: device pointer to dense populations
+ * f[sub][i][z][y][x] in the storage type `storage` (lbm_storage; offset types hold
+ * d = f/w - 1), i in the library's direction order; out5: device pointer to 5 doubles;
+ * cuda_stream: the stream to run on (NULL: legacy default).  Asynchronous: returns after
+ * queueing two kernels.  Its scratch is a fixed 160 KiB device array inside the library
+ * (4096 partial sums of 8192 sites each), which every device that loads the library holds
+ * until exit; grids with 2*nx*ny*nz > 33,554,432 sites are rejected with LBM_EINVAL.  The
+ * first call on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls share the array,
+ * which keeps the last call's contents; calls that overlap on the GPU (different streams)
+ * race on it.  Returns LBM_EINVAL for bad arguments, LBM_ECUDA if a launch fails. */
+lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz, double* out5, void* cuda_stream);
+
 /* ---- serving: continuous batching of independent cases on one GPU --------------------
  *
  * A server keeps many cases (each an lbm_config with its own grid, tau, faces and storage)
