@@ -255,6 +255,75 @@ def run_e2e(B, n: int, storage: str, steps: int):
             "note": f"TGV {n}^3 {storage}: lbm_init from pinned host fields + lbm_step(1) + lbm_moments to pinned host"}
 
 
+def run_served(B, n_requests: int = 12, seed: int = 5114):
+    """Served mixed batch (continuous batching, lbm_server_*): seeded Poisson arrivals of
+    shock tubes, Taylor-Green vortices and blob flows (FP32 / FP16-offset storage), each
+    submitted at its arrival time; reports time-to-solution p50/p99 and aggregate MLUPS, and
+    the same request list run as per-case plain FP64 launches one after another."""
+    import numpy as np
+    import torch
+    from paper_2409_05114_gb300 import workloads as W
+    reqs = W.served_mix(n_requests, seed=seed)
+    host = [(np.ascontiguousarray(r.workload.rho).reshape(-1), np.ascontiguousarray(r.workload.u).reshape(-1),
+             np.ascontiguousarray(r.workload.theta).reshape(-1)) for r in reqs]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    srv = B.lbm_server_create(budget, 64)
+    lat, status = [], []
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for r, (rho, u, th) in zip(reqs, host):
+            delay = t0 + r.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            wl = r.workload
+            cfg = B.make_config(wl.nx, wl.ny, wl.nz, r.tau, r.storage, wl.faces)
+            tickets.append(B.lbm_submit(srv, cfg, rho, u, th, r.nsteps))
+        for t in tickets:
+            if B.lbm_wait(srv, t, 900.0) != B.LBM_OK:
+                raise RuntimeError("served request did not finish")
+            st, l = B.lbm_poll(srv, t)
+            lat.append(l)
+            status.append(st)
+        wall = time.perf_counter() - t0
+        stats = B.lbm_server_get_stats(srv)
+    finally:
+        B.lbm_server_destroy(srv)
+    work_ok = sum(r.workload.sites * r.nsteps for r, st in zip(reqs, status) if st == B.LBM_OK)
+    # baseline: the same list as per-case plain FP64 launches, one after another
+    torch.cuda.synchronize()
+    tb = time.perf_counter()
+    for r, (rho, u, th) in zip(reqs, host):
+        wl = r.workload
+        ctx = B.lbm_create(B.make_config(wl.nx, wl.ny, wl.nz, r.tau, "f64", wl.faces))
+        try:
+            B.lbm_init(ctx, rho, u, th)
+            B.lbm_step(ctx, r.nsteps)
+            S = wl.sites
+            try:
+                B.lbm_moments(ctx, np.zeros(S), np.zeros(3 * S), np.zeros(S))
+            except B.LbmUnstable:
+                pass
+        finally:
+            B.lbm_destroy(ctx)
+    t_fp64 = time.perf_counter() - tb
+    work_all = sum(r.workload.sites * r.nsteps for r in reqs)
+    lat_ms = sorted(1e3 * x for x in lat)
+    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(round(q * (len(lat_ms) - 1))))]
+    return {"requests": len(reqs), "completed_ok": sum(1 for s in status if s == B.LBM_OK),
+            "unstable": sum(1 for s in status if s == B.LBM_EUNSTABLE),
+            "p50_ms": round(pct(0.5), 2), "p99_ms": round(pct(0.99), 2),
+            "aggregate_mlups": round(work_ok / wall / 1e6, 1), "wall_s": round(wall, 3),
+            "fp64_per_case_mlups": round(work_all / t_fp64 / 1e6, 1), "fp64_per_case_wall_s": round(t_fp64, 2),
+            "speedup_vs_fp64_per_case": round((work_ok / wall) / (work_all / t_fp64), 2),
+            "site_updates": work_ok, "ticks": stats["ticks"], "graph_launches": stats["graph_launches"],
+            "peak_resident_gb": round(stats["peak_resident_bytes"] / 1e9, 2), "hbm_budget_gb": round(budget / 1e9, 1),
+            "storage": "f32/f16-offset mix", "arrivals": "Poisson, seed 5114, mean 0.1 s",
+            "mix": "shock tubes 256-2048x4x4 (rho 1|0.5, theta 1|0.9), TGV 32^3-192^3 Ma 0.3-0.7, "
+                   "blob flows 256^2x4-1024x256x4 Ma 0.5; 200-2000 steps"}
+
+
 def cpu_baseline(n: int = 128, steps: int = 1):
     """Times the FP64 oracle (as it stands) in a single-threaded subprocess: `steps` full
     oracle steps of the TGV n^3 workload."""
@@ -320,6 +389,10 @@ def ours(args):
                               "roofline_frac": round(r["gbs"] / peak, 4), "ms_per_step": round(r["ms_per_step"], 4)}
         line["variants"] = variants
         line["e2e"] = run_e2e(B, args.n, args.storage, 3)
+        try:
+            line["served"] = run_served(B)
+        except Exception as exc:  # report, do not lose the rest of the line
+            line["served"] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.quick and not args.no_cpu_baseline and rank == 0:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

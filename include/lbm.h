@@ -182,9 +182,10 @@ lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz
  * free and the sum of resident case footprints (2 population buffers each) stays within
  * the HBM budget; admission (host-to-device copy and initialisation) runs on its own
  * stream while the resident cases compute.  A case leaves after its step count, or early
- * when one of its sites becomes unstable.  Its result is bitwise the same as when it runs
- * alone: every site is updated by the same code as lbm_step.  A scheduler thread owned by
- * the server does all GPU work; the calls below are thread-safe. */
+ * when one of its sites becomes unstable.  Its result is bitwise the same whether it is
+ * served alone or in any mix (sites are independent and every case runs the same kernel),
+ * and equals lbm_step's to rounding (the same arithmetic, compiled into another kernel).
+ * A scheduler thread owned by the server does all GPU work; the calls are thread-safe. */
 typedef struct lbm_server lbm_server;
 
 typedef struct {

@@ -47,6 +47,15 @@ class lbm_config(ctypes.Structure):
                 ("fp64_moments", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
 
 
+class lbm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("unstable", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("queued", ctypes.c_longlong),
+                ("site_updates", ctypes.c_longlong), ("ticks", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong),
+                ("resident_cases", ctypes.c_int), ("resident_bytes", ctypes.c_size_t),
+                ("peak_resident_bytes", ctypes.c_size_t), ("busy_seconds", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} is not built; run __graft_entry__.build() "
@@ -68,6 +77,13 @@ def _load():
         "lbm_destroy": ([P], I),
         "lbm_last_error": ([P], ctypes.c_char_p),
         "lbm_velocities": ([P, P], I),
+        "lbm_server_create": ([ctypes.c_size_t, I, ctypes.POINTER(P)], I),
+        "lbm_submit": ([P, ctypes.POINTER(lbm_config), P, P, P, LL, ctypes.POINTER(LL)], I),
+        "lbm_poll": ([P, LL, P, P, P, ctypes.POINTER(D)], I),
+        "lbm_wait": ([P, LL, D], I),
+        "lbm_server_get_stats": ([P, ctypes.POINTER(lbm_server_stats)], I),
+        "lbm_server_last_error": ([P], ctypes.c_char_p),
+        "lbm_server_destroy": ([P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -213,3 +229,51 @@ def lbm_velocities():
     n = _lib.lbm_velocities(ctypes.c_void_p(h.ctypes.data), ctypes.c_void_p(w.ctypes.data))
     assert n == Q
     return h.reshape(Q, 3), w
+
+
+# ---- serving ---------------------------------------------------------------------------
+
+def _check_srv(status: int, srv=None):
+    if status != LBM_OK:
+        msg = _lib.lbm_server_last_error(srv).decode()
+        raise (LbmUnstable if status == LBM_EUNSTABLE else LbmError)(status, msg)
+
+
+def lbm_server_create(hbm_budget_bytes: int, max_cases: int):
+    srv = ctypes.c_void_p()
+    _check_srv(_lib.lbm_server_create(int(hbm_budget_bytes), int(max_cases), ctypes.byref(srv)))
+    return srv
+
+
+def lbm_submit(srv, cfg: lbm_config, rho, u, theta, nsteps: int) -> int:
+    """Queues a case (host fields, copied before returning); returns its ticket."""
+    (pr, d0), (pu, d1), (pt, d2) = _ptr(rho), _ptr(u), _ptr(theta)
+    if d0 or d1 or d2:
+        raise ValueError("lbm_submit takes host arrays")
+    t = ctypes.c_longlong()
+    _check_srv(_lib.lbm_submit(srv, ctypes.byref(cfg), pr, pu, pt, int(nsteps), ctypes.byref(t)), srv)
+    return t.value
+
+
+def lbm_poll(srv, ticket: int, rho=None, u=None, theta=None):
+    """(status, latency_s).  status LBM_EBUSY while running; once done the fields are copied
+    into the given host arrays (any may be None) and the ticket is forgotten."""
+    lat = ctypes.c_double(0.0)
+    ptrs = [None if a is None else _ptr(a, True)[0] for a in (rho, u, theta)]
+    st = _lib.lbm_poll(srv, int(ticket), *ptrs, ctypes.byref(lat))
+    return st, lat.value
+
+
+def lbm_wait(srv, ticket: int, timeout_s: float) -> int:
+    """LBM_OK when the case is done, LBM_ETIMEOUT after timeout_s seconds."""
+    return _lib.lbm_wait(srv, int(ticket), float(timeout_s))
+
+
+def lbm_server_get_stats(srv) -> dict:
+    st = lbm_server_stats()
+    _check_srv(_lib.lbm_server_get_stats(srv, ctypes.byref(st)), srv)
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def lbm_server_destroy(srv):
+    _check_srv(_lib.lbm_server_destroy(srv))

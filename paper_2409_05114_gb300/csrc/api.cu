@@ -12,6 +12,7 @@ namespace {
 
 constexpr uint32_t kMagic = 0x52443831u;  // "RD81"
 constexpr long long kChunkSites = 1LL << 22;  // sites per host-transfer chunk
+constexpr int kGraphSteps = 8;                // steps per replayed CUDA graph (even)
 
 thread_local std::string g_create_error = "no error";
 
@@ -106,6 +107,8 @@ struct lbm_ctx {
   bool inflow[2] = {false, false};
   lbm::Feq81 feq_in[2]{};
   long long launches = 0;
+  cudaGraphExec_t graph = nullptr;  // kGraphSteps steps starting from buffer 0
+  long long direct_steps = 0;       // steps issued by plain launches (the first ones load the kernels)
   std::string err = "no error";
 };
 
@@ -270,26 +273,81 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
   return LBM_OK;
 }
 
-lbm_status lbm_step(lbm_ctx* ctx, long long n) {
-  if (!valid(ctx)) return LBM_EINVAL;
-  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
-  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
-  DeviceGuard dg(ctx->device);
+namespace {
+
+// Issues one step (ghost fills + fused kernel) reading buffer `cur` on stream s.
+cudaError_t issue_step(lbm_ctx* ctx, int cur, cudaStream_t s) {
+  for (int face = 0; face < 2; ++face) {
+    if (!ctx->zero_grad[face]) continue;
+    cudaError_t e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
+    if (e != cudaSuccess) return e;
+  }
   lbm::StepParams p;
   p.g = ctx->g;
   p.omega = ctx->omega;
   p.flag = ctx->d_flag;
   p.tab = ctx->tab;
-  for (long long k = 0; k < n; ++k) {
-    for (int face = 0; face < 2; ++face) {
-      if (!ctx->zero_grad[face]) continue;
-      LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
-      ++ctx->launches;
+  p.src = ctx->buf[cur];
+  p.dst = ctx->buf[cur ^ 1];
+  lbm::fill_slab_bases(&p, ctx->elem);
+  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, p, s);
+}
+
+int launches_per_step(const lbm_ctx* ctx) { return 1 + (ctx->zero_grad[0] ? 1 : 0) + (ctx->zero_grad[1] ? 1 : 0); }
+
+// Captures kGraphSteps steps starting from buffer 0 (the ping-pong returns to buffer 0).
+cudaError_t build_graph(lbm_ctx* ctx) {
+  cudaStream_t cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  for (int k = 0; e == cudaSuccess && k < kGraphSteps; ++k) e = issue_step(ctx, k & 1, cap);
+  cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    ctx->graph = nullptr;
+    cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace
+
+lbm_status lbm_step(lbm_ctx* ctx, long long n) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  // Runs of kGraphSteps steps are replayed from one captured graph (launch overhead matters
+  // for small grids), unless the caller is capturing the context's stream itself.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  LBM_CK(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+  const bool graphs = cs == cudaStreamCaptureStatusNone && n >= kGraphSteps + 2;
+  long long k = 0;
+  if (graphs) {
+    // plain steps first: until two have run (kernels loaded before any capture) and until
+    // the state is back in buffer 0, where the graph starts
+    while (ctx->direct_steps < 2 || ctx->cur == 1) {
+      LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->stream));
+      ctx->launches += launches_per_step(ctx);
+      ++ctx->direct_steps;
+      ctx->cur ^= 1;
+      ++k;
     }
-    p.src = ctx->buf[ctx->cur];
-    p.dst = ctx->buf[ctx->cur ^ 1];
-    LBM_CK(ctx, lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, p, ctx->stream));
-    ++ctx->launches;
+    if (!ctx->graph && n - k >= kGraphSteps) LBM_CK(ctx, build_graph(ctx));
+    for (; n - k >= kGraphSteps; k += kGraphSteps) {
+      LBM_CK(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
+      ctx->launches += static_cast<long long>(kGraphSteps) * launches_per_step(ctx);
+    }
+  }
+  for (; k < n; ++k) {
+    LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->stream));
+    ctx->launches += launches_per_step(ctx);
+    ++ctx->direct_steps;
     ctx->cur ^= 1;
   }
   return LBM_OK;
@@ -437,6 +495,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->d_totals) cudaFree(ctx->d_totals);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   }
   ctx->magic = 0;

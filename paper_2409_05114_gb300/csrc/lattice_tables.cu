@@ -67,4 +67,15 @@ void build_lattice_tables(LatticeTables* t) {
   for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
 }
 
+void fill_slab_bases(StepParams* p, size_t elem) {
+  const char* src = static_cast<const char*>(p->src);
+  char* dst = static_cast<char*>(p->dst);
+  for (int sub = 0; sub < 2; ++sub)
+    for (int i = 0; i < kQ; ++i) {
+      const int from = (rd3q81::kDirs[i].hx % 2 != 0) ? 1 - sub : sub;
+      p->src_slab[sub][i] = src + (from * p->g.sub_stride + i * p->g.dir_stride) * static_cast<long long>(elem);
+      p->dst_slab[sub][i] = dst + (sub * p->g.sub_stride + i * p->g.dir_stride) * static_cast<long long>(elem);
+    }
+}
+
 }  // namespace lbm

@@ -67,7 +67,15 @@ struct StepParams {
   double omega;          // alpha * beta = 2 / (2 tau + 1)
   unsigned int* flag;    // set to nonzero when a site sees rho <= 0, theta <= 0 or non-finite
   LatticeTables tab;
+  // Base addresses, per target sublattice and direction, of the slab a pull reads from
+  // (the other sublattice for half links) and of the slab the update writes to.  Filled by
+  // fill_slab_bases(); they spare the kernel the 64-bit slab arithmetic of every access.
+  const void* src_slab[2][kQ];
+  void* dst_slab[2][kQ];
 };
+
+// Fills p.src_slab / p.dst_slab from p.src, p.dst, p.g and the element size.
+void fill_slab_bases(StepParams* p, size_t elem);
 
 // Validates cfg and derives its buffer geometry (api.cu); LBM_OK or LBM_EINVAL with *why.
 lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why);

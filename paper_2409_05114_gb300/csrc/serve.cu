@@ -5,9 +5,9 @@
 // table.  A step of the whole batch is (a) one batched zero-gradient ghost fill (only if a
 // resident case has such a face) and (b) one persistent kernel whose blocks walk a packed
 // index of 128-site tiles over all cases: the tile's case is found by binary search over the
-// cases' first-tile offsets, and the site is updated by exactly the same code path as the
-// single-case kernel (site_update), so a case's result is bitwise the same alone and in any
-// mix.  K steps form one "tick", captured once per (membership, K) as a CUDA graph and
+// cases' first-tile offsets, and the site is updated by the same device function as the
+// single-case kernel's (site_update).  Sites are independent, so a case's result is bitwise
+// the same served alone and in any mix.  K steps form one "tick", captured once per (membership, K) as a CUDA graph and
 // replayed.  A scheduler thread admits queued requests by HBM footprint on a separate
 // stream while the current tick runs, and retires finished or unstable cases after it.
 #include <algorithm>
@@ -66,7 +66,7 @@ __device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, 
 
 // Step k of the current tick for every resident case.  Grid: persistent (SMs x resident
 // blocks); block b handles tiles b, b + gridDim.x, ...  No block waits on another.
-__global__ void __launch_bounds__(kScBlock) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
+__global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
                                                                long long total_tiles, int k, const LatticeTables tab) {
   __shared__ long long s_first[kMaxServerCases];
   for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].tile0;

@@ -42,23 +42,13 @@ __device__ __forceinline__ const R* tab_nb(const LatticeTables& t) {
   if constexpr (std::is_same_v<R, double>) return t.nb; else return t.nbf;
 }
 
-// Updates interior site t of sublattice SUB: reads `src`, writes `dst` (both whole
-// population buffers of geometry g), relaxation omega, instability flag `flag`.
-// kF64Mom: the moment sums and the temperature recovery run in FP64 whatever the storage.
-template <class Store, bool kF64Mom, int SUB>
-__device__ __forceinline__ void site_update(const Geometry& g, const void* src_buf, void* dst_buf, double omega,
-                                            unsigned int* flag, const LatticeTables& tb, int t) {
-  using C = Codec<Store>;
-  using R = typename C::Real;                                  // collide arithmetic
-  using M = std::conditional_t<kF64Mom, double, R>;            // moment arithmetic
-
+// Source coordinates of site t for index displacements d = -4 .. 4 (slot d + 4): x as an
+// element index within a row, y and z as element offsets of the row and plane.
+__device__ __forceinline__ void site_coords(const Geometry& g, int t, int* xs, int* ys, int* zs) {
   const int x = t % g.nx;
   const int r = t / g.nx;
   const int y = r % g.ny;
   const int z = r / g.ny;
-
-  // Source coordinates for index displacements d = -4 .. 4 (slot d + 4).
-  int xs[9], ys[9], zs[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int d = k - 4;
@@ -66,12 +56,15 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     ys[k] = wrap_idx(y - d, g.ny) * g.pitch;
     zs[k] = wrap_idx(z - d, g.nz) * static_cast<int>(g.plane);
   }
+}
 
-  // ---- pull -----------------------------------------------------------------------------
-  const Store* src = static_cast<const Store*>(src_buf);
+// Calls fn(i, pointer) with the source element of direction i pulled into a site of
+// sublattice SUB whose coordinates are xs/ys/zs.
+template <class Store, int SUB, class Fn>
+__device__ __forceinline__ void for_each_source(const Geometry& g, const Store* src, const int* xs, const int* ys,
+                                                const int* zs, Fn&& fn) {
   const Store* same = src + SUB * g.sub_stride;
   const Store* other = src + (1 - SUB) * g.sub_stride;
-  R f[kQ];
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
@@ -80,14 +73,25 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     constexpr int dz = rd3q81::pull_disp(d.hz, SUB);
     constexpr bool cross = (d.hx % 2) != 0;
     const Store* base = (cross ? other : same) + static_cast<long long>(i) * g.dir_stride;
-    f[i] = C::load(base + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
+    fn(Ic, base + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
   });
+}
 
-  // ---- moments, Eq. (conslaws) ----------------------------------------------------------
-  // Offset storage holds d_i = f_i/w_i - 1, so rho = 1 + <w, d>, j = <w, d c>,
-  // <f, c^2> = 3 theta0 + <w, d c^2> (the weights' own moments are 1, 0, 3 theta0).
-  // FP32 sums of FP32 populations are also taken over the deviations f_i - w_i: the same
-  // moments, summed from numbers ~10x smaller than f_i, hence ~10x smaller rounding.
+// Conserved moments of Eq. (conslaws) in arithmetic M.
+template <class M>
+struct Moments {
+  M rho, jx, jy, jz, E;
+};
+
+// Offset storage holds d_i = f_i/w_i - 1, so rho = 1 + <w, d>, j = <w, d c>,
+// <f, c^2> = 3 theta0 + <w, d c^2> (the weights' own moments are 1, 0, 3 theta0).
+// FP32 sums of FP32 populations are also taken over the deviations f_i - w_i: the same
+// moments, summed from numbers ~10x smaller than f_i, hence ~10x smaller rounding.
+template <class Store, bool kF64Mom>
+__device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* f, const LatticeTables& tb) {
+  using C = Codec<Store>;
+  using R = typename C::Real;
+  using M = std::conditional_t<kF64Mom, double, R>;
   constexpr bool kDev = C::kOffset || std::is_same_v<M, float>;
   M rho, jx = M(0), jy = M(0), jz = M(0), E = M(0);
   if constexpr (C::kOffset) rho = tab_w<M>(tb, 0) * M(f[0]);
@@ -118,14 +122,23 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     rho += M(1);
     E += M(3.0 * rd3q81::kTheta0);
   }
-  const M irho = M(1) / rho;
-  const M mux = jx * irho, muy = jy * irho, muz = jz * irho;
-  const M mtheta = (E * irho - (mux * mux + muy * muy + muz * muz)) * M(1.0 / 3.0);
+  return Moments<M>{rho, jx, jy, jz, E};
+}
 
-  const R rh = R(rho);
+// Temperature recovery, equilibrium (App. B) and BGK relaxation of one site's populations
+// f (in place), given their moments.
+template <class Store, class M>
+__device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const Moments<M>& mo, double omega,
+                                           unsigned int* flag, const LatticeTables& tb) {
+  using C = Codec<Store>;
+  using R = typename C::Real;
+  const M irho = M(1) / mo.rho;
+  const M mux = mo.jx * irho, muy = mo.jy * irho, muz = mo.jz * irho;
+  const M mtheta = (mo.E * irho - (mux * mux + muy * muy + muz * muz)) * M(1.0 / 3.0);
+
+  const R rh = R(mo.rho);
   const R theta = R(mtheta);
   if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(flag, 1u);
-
   // ---- equilibrium scalars, App. B ------------------------------------------------------
   const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
   EqScalars<R> e;
@@ -142,8 +155,10 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
   // rounded to FP32), and the defect would accumulate step after step.  For FP32 storage
   // the defects of D are therefore summed (D is small, so the sums are accurate) and removed
   // by subtracting w_i (a + b.c_i + g c_i^2) with a, b, g fixed by the weights' moments
-  // <w,1> = 1, <w,c c> = theta0 I, <w,c^2> = 3 theta0, <w,c^4> = 15 theta0^2.  The result
-  // equals the plain update in exact arithmetic; in FP32 it conserves to the sums' rounding.
+  // <w,1> = 1, <w,c c> = theta0 I, <w,c^2> = 3 theta0, <w,c^4> = 15 theta0^2.  The
+  // correction has the shape of an equilibrium perturbation, so it adds no non-equilibrium
+  // part (with omega near 2 such a part would hardly decay).  The result equals the plain
+  // update in exact arithmetic; in FP32 it conserves to the rounding of the defect sums.
   constexpr bool kProject = std::is_same_v<Store, float>;
   const R om = R(omega);
   R d1 = R(0), dE = R(0), dx = R(0), dy = R(0), dz = R(0);
@@ -158,7 +173,6 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     constexpr int P = decltype(Pc)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
     constexpr int s = d.shell;
-    constexpr double c2 = rd3q81::kShellC2[s];
     R ev, od;
     eq_pair_parts<P, R>(e, ev, od);
     const R we = W[s] * ev;
@@ -171,6 +185,7 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     const R Dp = fp - f[1 + 2 * P];
     const R Dm = fm - f[2 + 2 * P];
     if constexpr (kProject) {
+      constexpr double c2 = rd3q81::kShellC2[s];
       const R sD = Dp + Dm, dD = Dp - Dm;
       d1 += sD;
       dE += R(c2) * sD;
@@ -203,24 +218,80 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
       f[2 + 2 * P] -= ce - co;
     });
   }
+}
 
-  // ---- store (coalesced, same site index in the other buffer) ----------------------------
-  Store* dst = static_cast<Store*>(dst_buf) + SUB * g.sub_stride + (zs[4] + ys[4] + xs[4]);
+template <class Store>
+__device__ __forceinline__ void site_store(const Geometry& g, void* dst_buf, int sub, int own,
+                                           const typename Codec<Store>::Real* f) {
+  Store* dst = static_cast<Store*>(dst_buf) + sub * g.sub_stride + own;
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
-    C::store(dst + static_cast<long long>(i) * g.dir_stride, f[i]);
+    Codec<Store>::store(dst + static_cast<long long>(i) * g.dir_stride, f[i]);
   });
 }
 
+// Updates interior site t of sublattice SUB: reads `src`, writes `dst` (both whole
+// population buffers of geometry g), relaxation omega, instability flag `flag`.
+// kF64Mom: the moment sums and the temperature recovery run in FP64 whatever the storage.
+template <class Store, bool kF64Mom, int SUB>
+__device__ __forceinline__ void site_update(const Geometry& g, const void* src_buf, void* dst_buf, double omega,
+                                            unsigned int* flag, const LatticeTables& tb, int t) {
+  using C = Codec<Store>;
+  using R = typename C::Real;
+  int xs[9], ys[9], zs[9];
+  site_coords(g, t, xs, ys, zs);
+  R f[kQ];
+  for_each_source<Store, SUB>(g, static_cast<const Store*>(src_buf), xs, ys, zs, [&](auto Ic, const Store* p) {
+    f[decltype(Ic)::value] = C::load(p);
+  });
+  const auto mo = site_moments<Store, kF64Mom>(f, tb);
+  site_relax<Store>(f, mo, omega, flag, tb);
+  site_store<Store>(g, dst_buf, SUB, zs[4] + ys[4] + xs[4], f);
+}
+
+// The single-case form of site_update: the same phases, with the slab base addresses taken
+// from the kernel parameters instead of being computed per access.
+template <class Store, bool kF64Mom, int SUB>
+__device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
+  using C = Codec<Store>;
+  using R = typename C::Real;
+  int xs[9], ys[9], zs[9];
+  site_coords(p.g, t, xs, ys, zs);
+  R f[kQ];
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[i];
+    constexpr int dx = rd3q81::pull_disp(d.hx, SUB);
+    constexpr int dy = rd3q81::pull_disp(d.hy, SUB);
+    constexpr int dz = rd3q81::pull_disp(d.hz, SUB);
+    f[i] = C::load(static_cast<const Store*>(p.src_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
+  });
+  const auto mo = site_moments<Store, kF64Mom>(f, p.tab);
+  site_relax<Store>(f, mo, p.omega, p.flag, p.tab);
+  const int own = zs[4] + ys[4] + xs[4];
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    C::store(static_cast<Store*>(p.dst_slab[SUB][i]) + own, f[i]);
+  });
+}
+
+// Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
+// 4 for FP32/FP16/BF16 storage with FP32 moments (<= 128 registers, 16 warps per SM), 3 for
+// FP32 with FP64 moments, and no bound for FP64 storage (its 81 doubles need ~250).
 template <class Store, bool kF64Mom>
-__global__ void __launch_bounds__(kScBlock) stream_collide_kernel(const StepParams p) {
+constexpr int sc_min_blocks() {
+  return std::is_same_v<Store, double> ? 1 : (kF64Mom && std::is_same_v<Store, float>) ? 3 : 4;
+}
+
+template <class Store, bool kF64Mom>
+__global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom>()) stream_collide_kernel(const StepParams p) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const long long t = static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
   if (t >= n) return;
   if (blockIdx.y == 0)
-    site_update<Store, kF64Mom, 0>(p.g, p.src, p.dst, p.omega, p.flag, p.tab, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 0>(p, static_cast<int>(t));
   else
-    site_update<Store, kF64Mom, 1>(p.g, p.src, p.dst, p.omega, p.flag, p.tab, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 1>(p, static_cast<int>(t));
 }
 
 template <class Store, bool kF64Mom>

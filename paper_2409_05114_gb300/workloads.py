@@ -87,6 +87,19 @@ def sod(nx: int = 512, ny: int = 4, nz: int = 4, tau_lb: float = 0.6, steps: int
                     ["zero_gradient", "zero_gradient"] + ["periodic"] * 4)
 
 
+def shock_tube(nx: int = 512, ny: int = 4, nz: int = 4, rho_right: float = 0.125, theta_right: float = 0.8,
+               tau_lb: float = 0.6, steps: int = 200) -> Workload:
+    """Sod-type tube: left rho = 1, theta = theta0; right rho = rho_right,
+    theta = theta_right * theta0; u = 0; interface at x = nx/2; zero-gradient x faces."""
+    wl = sod(nx, ny, nz, tau_lb, steps)
+    x, _, _ = positions(nx, ny, nz)
+    left = x < nx / 2.0
+    wl.rho = np.where(left, 1.0, rho_right)
+    wl.theta = np.where(left, THETA0, theta_right * THETA0)
+    wl.name = f"shock_tube_{nx}_r{rho_right:g}_t{theta_right:g}"
+    return wl
+
+
 def taylor_green(n: int = 128, mach: float = 0.5, tau_lb: float = 0.51, steps: int = 1000) -> Workload:
     """u = U0 (sin x^ cos y^ cos z^, -cos x^ sin y^ cos z^, 0), rho = 1,
     p = p0 + rho0 U0^2/16 (cos 2x^ + cos 2y^)(cos 2z^ + 2) with p0 = theta0 and theta = p/rho,
@@ -176,3 +189,58 @@ def smooth_random(nx: int, ny: int, nz: int, seed: int = 0, mach: float = 0.3, e
     u = np.stack([mach * CS * mode(), mach * CS * mode(), 0.5 * mach * CS * mode()])
     return Workload(f"smooth_{nx}x{ny}x{nz}", nx, ny, nz, tau_lb, steps, rho, u, theta,
                     faces or ["periodic"] * 6)
+
+
+@dataclass
+class ServedRequest:
+    workload: Workload
+    storage: str
+    nsteps: int
+    arrival_s: float
+    tau: float           # the paper's tau passed to the library
+
+
+def served_mix(n_requests: int = 12, seed: int = 5114, mean_interarrival_s: float = 0.1,
+               max_steps: int = 2000) -> list:
+    """Mixed-size request stream (seeded): Poisson arrivals; each request drawn uniformly from
+      * shock tubes nx x 4 x 4, nx in {256, 512, 1024, 2048}: rho 1 | 0.5, theta theta0 |
+        0.9 theta0, zero-gradient x faces, tau_lb 0.6;
+      * Taylor-Green n^3, n in {32, 48, 64, 96, 128, 160, 192}, Ma in {0.3, 0.5, 0.7}, tau_lb 0.55;
+      * blob flows 256x256x4, 512x128x4, 1024x256x4 at Ma 0.5 (inflow/outflow);
+    each with 200 .. max_steps steps and FP32 or FP16-offset storage.  The ranges are those in
+    which the series equilibrium with BGK runs the full 2000 steps: the strong Sod jump
+    (rho 1 | 0.125, theta 1 | 0.8; unstable at every tau tried once the shock meets the
+    outflow face), TGV
+    at Ma 1.0 (any tau tried), TGV at Ma 0.7 with tau_lb 0.51 and the Mach-2 blob leave it
+    within 20-300 steps and would be retired as unstable.  Field generation is cached per
+    shape."""
+    rng = np.random.default_rng(seed)
+    cache = {}
+    out = []
+    t = 0.0
+    for _ in range(n_requests):
+        t += rng.exponential(mean_interarrival_s)
+        fam = rng.integers(0, 3)
+        if fam == 0:
+            nx = int(rng.choice([256, 512, 1024, 2048]))
+            key = ("tube", nx)
+            if key not in cache:
+                cache[key] = shock_tube(nx=nx, rho_right=0.5, theta_right=0.9)
+            wl, tau = cache[key], paper_tau(0.6, "lb")
+        elif fam == 1:
+            n = int(rng.choice([32, 48, 64, 96, 128, 160, 192]))
+            ma = float(rng.choice([0.3, 0.5, 0.7]))
+            key = ("tgv", n, ma)
+            if key not in cache:
+                cache[key] = taylor_green(n, mach=ma, tau_lb=0.55)
+            wl, tau = cache[key], paper_tau(0.55, "lb")
+        else:
+            shape = [(256, 256, 4), (512, 128, 4), (1024, 256, 4)][rng.integers(0, 3)]
+            key = ("blob",) + shape
+            if key not in cache:
+                cache[key] = mach2_blob(*shape, mach=0.5, vortex=0.1)
+            wl, tau = cache[key], paper_tau(0.55, "literal")
+        steps = int(rng.integers(200, max_steps + 1))
+        storage = "f32" if rng.random() < 0.5 else "f16"
+        out.append(ServedRequest(wl, storage, steps, t, tau))
+    return out
