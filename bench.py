@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--storage", default="f32", choices=sorted(BYTES))
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--served-only", type=int, default=0, metavar="N",
+                   help="run only the served mixed batch with N requests (no FP64 comparison)")
     return p.parse_args()
 
 
@@ -134,6 +136,32 @@ def gpu_index_for_smi(local_rank: int) -> str:
     if vis:
         return vis.split(",")[local_rank].strip()
     return str(local_rank)
+
+
+KERNEL_SOURCES = ("stream_collide.cuh", "device_common.cuh", "lbm_internal.h", "rd3q81.h", "sc_f32.cu")
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2409_05114_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(storage: str, sites: int):
+    """DRAM bytes (read + write) of one fused-kernel launch, from the committed ncu record
+    (bytes per site measured on a smaller grid, scaled by the sites); None if the record is
+    missing or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != kernel_source_sha():
+        return None
+    k = rec.get("kernels", {}).get(storage)
+    return None if k is None else int(round(k["dram_bytes_per_site"] * sites))
 
 
 def measured_peaks():
@@ -255,7 +283,7 @@ def run_e2e(B, n: int, storage: str, steps: int):
             "note": f"TGV {n}^3 {storage}: lbm_init from pinned host fields + lbm_step(1) + lbm_moments to pinned host"}
 
 
-def run_served(B, n_requests: int = 12, seed: int = 5114):
+def run_served(B, n_requests: int = 12, seed: int = 5114, compare_fp64: bool = True):
     """Served mixed batch (continuous batching, lbm_server_*): seeded Poisson arrivals of
     shock tubes, Taylor-Green vortices and blob flows (FP32 / FP16-offset storage), each
     submitted at its arrival time; reports time-to-solution p50/p99 and aggregate MLUPS, and
@@ -291,6 +319,11 @@ def run_served(B, n_requests: int = 12, seed: int = 5114):
     finally:
         B.lbm_server_destroy(srv)
     work_ok = sum(r.workload.sites * r.nsteps for r, st in zip(reqs, status) if st == B.LBM_OK)
+    lat_ms = sorted(1e3 * x for x in lat)
+    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(round(q * (len(lat_ms) - 1))))]
+    if not compare_fp64:
+        return {"requests": len(reqs), "p50_ms": round(pct(0.5), 2), "p99_ms": round(pct(0.99), 2),
+                "aggregate_mlups": round(work_ok / wall / 1e6, 1)}
     # baseline: the same list as per-case plain FP64 launches, one after another
     torch.cuda.synchronize()
     tb = time.perf_counter()
@@ -309,8 +342,6 @@ def run_served(B, n_requests: int = 12, seed: int = 5114):
             B.lbm_destroy(ctx)
     t_fp64 = time.perf_counter() - tb
     work_all = sum(r.workload.sites * r.nsteps for r in reqs)
-    lat_ms = sorted(1e3 * x for x in lat)
-    pct = lambda q: lat_ms[min(len(lat_ms) - 1, int(round(q * (len(lat_ms) - 1))))]
     return {"requests": len(reqs), "completed_ok": sum(1 for s in status if s == B.LBM_OK),
             "unstable": sum(1 for s in status if s == B.LBM_EUNSTABLE),
             "p50_ms": round(pct(0.5), 2), "p99_ms": round(pct(0.99), 2),
@@ -355,6 +386,9 @@ def ours(args):
     rank, world, local = dist_setup(args)
     torch.cuda.set_device(local)
     from paper_2409_05114_gb300 import binding as B
+    if args.served_only:
+        print(json.dumps({"served": run_served(B, args.served_only, compare_fp64=False)}), flush=True)
+        return
 
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(gpu_index_for_smi(local))
@@ -371,7 +405,7 @@ def ours(args):
                    "streaming": "pull, ping-pong", "tau_lb": 0.51, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (one step moves %.0f GB)" % (head["bytes_per_site"] * head["sites"] / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"]),
                      "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                      "bytes_per_site": head["bytes_per_site"]},
         "gpu_launches": head["launches"],
