@@ -18,6 +18,9 @@ read against the paper line by line:
 * ``equilibrium``         App. B, "Discrete equilibrium at nonzero velocity": f~eq with
                           f^(2), f^(3), R-bar and the tensor R-bar_{kappa alpha zeta eta},
                           the last two as explicit 81-term sums over W~/rho.
+* ``entropic_equilibrium`` Sec. III: the exact minimiser of H = <f, log(f/w) - 1>, i.e.
+                          w rho exp(mu + zeta.c + gamma c^2), by Newton on the paper's 5x5
+                          moment system; ``boltzmann_h`` is H itself.
 * ``stream``              Sec. II, Eq. (discretelbm), left side: f_i moves by c_i in one
                           step.  Half-integer links join the primary lattice (P, integer
                           positions) and the replica lattice (R, positions + (1/2,1/2,1/2)),
@@ -244,6 +247,94 @@ def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice 
           + (5.0 * xi * q * Rb - Rcontr) / (6.0 * th ** 2))
     feq = W * (1.0 + f1 + f2 + f3)
     return feq.reshape((lat.q,) + S)
+
+
+def entropic_equilibrium(rho, u, theta, lat: Lattice | None = None, tol: float = 1e-12,
+                         max_iter: int = 100):
+    """Exact discrete entropic equilibrium of Sec. III:
+
+        f_i = w_i rho exp(mu + zeta . c_i + gamma c_i^2),
+
+    the minimiser of H = <f, log(f/w) - 1> under <f, {1, c, c^2}> = {rho, rho u,
+    rho u^2 + 3 rho theta}.  The multipliers are found as the paper describes: with a guess
+    f~ = w rho exp(mu0 + zeta0.c + gamma0 c^2), linearise exp(x) ~ 1 + x in the correction
+    (mu^, zeta^, gamma^), solve the 5x5 system whose matrix is <f~, phi_a phi_b> and whose
+    right side is (target moments - <f~, phi_a>), phi = (1, c_x, c_y, c_z, c^2), add the
+    correction and repeat (Newton's method on the multipliers).  The first guess is the
+    continuous Maxwellian's multipliers relative to w ~ exp(-c^2/(2 theta0)):
+    mu0 = -(3/2) ln(theta/theta0) - u^2/(2 theta), zeta0 = u/theta,
+    gamma0 = 1/(2 theta0) - 1/(2 theta).
+
+    Safeguard (not in the paper, inactive whenever the full step works): the correction is
+    the Newton step of the convex dual L(lambda) = <w rho exp(phi.lambda), 1> - lambda.target;
+    while the moment residual is above 1e-6, a step that would not decrease L is halved
+    until it does.  Converged when the
+    moment residual is below tol relative to rho (mass, momentum) and to the energy; one
+    more full step then takes the multipliers to round-off.
+
+    Inputs over sites (rho, theta [n], u [3, n]); returns (feq [81, n], multipliers [5, n],
+    iterations used).  Sites that do not converge within max_iter are NaN."""
+    lat = lat or velocity_set()
+    rho = np.asarray(rho, dtype=np.float64).reshape(-1)
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    u1 = np.asarray(u, dtype=np.float64).reshape(3, -1)
+    n = rho.size
+    phi = np.concatenate([np.ones((lat.q, 1)), lat.c, lat.c2[:, None]], axis=1)      # [81, 5]
+    q = (u1 ** 2).sum(axis=0)
+    target = np.stack([rho, rho * u1[0], rho * u1[1], rho * u1[2], rho * q + 3.0 * rho * th])  # [5, n]
+    scale = np.stack([rho, rho, rho, rho, target[4]])
+    lam = np.stack([-1.5 * np.log(th / lat.theta0) - q / (2.0 * th), u1[0] / th, u1[1] / th, u1[2] / th,
+                    0.5 / lat.theta0 - 0.5 / th])
+
+    def fdist(l):
+        return lat.w[:, None] * rho * np.exp(phi @ l)
+
+    def dual(f, l):
+        return f.sum(axis=0) - (l * target).sum(axis=0)
+
+    done = np.zeros(n, dtype=bool)
+    failed = np.zeros(n, dtype=bool)
+    final = np.zeros(n, dtype=bool)    # converged sites take one more full step
+    used = 0
+    with np.errstate(over="ignore", invalid="ignore"):
+        for it in range(max_iter):
+            used = it + 1
+            f = fdist(lam)
+            r = target - phi.T @ f                                                      # [5, n]
+            small = np.all(np.abs(r) <= tol * scale, axis=0)
+            done |= final
+            final = small & ~done
+            active = ~done & ~failed
+            if not active.any():
+                break
+            J = np.einsum("ia,ib,in->nab", phi, phi, f)                                # [n, 5, 5]
+            good = np.all(np.isfinite(J), axis=(1, 2)) & (np.abs(np.linalg.det(J)) > 0)
+            failed |= active & ~good
+            J[~good] = np.eye(5)
+            step = np.linalg.solve(J, np.where(good, r, 0.0).T[:, :, None])[:, :, 0].T  # [5, n]
+            # full steps once the residual is in Newton's quadratic range (where the dual's
+            # decrease is below its own rounding); the safeguard only acts far from it
+            near = np.all(np.abs(r) <= 1e-6 * scale, axis=0)
+            L0 = dual(f, lam)
+            t = np.ones(n)
+            for _ in range(60):
+                trial = lam + t * step
+                Lt = dual(fdist(trial), trial)
+                ok = near | (np.isfinite(Lt) & (Lt <= L0 - 1e-4 * t * (r * step).sum(axis=0)))
+                if (ok | ~active).all():
+                    break
+                t = np.where(ok, t, 0.5 * t)
+            lam = np.where(active & good, lam + t * step, lam)
+    f = fdist(lam)
+    f[:, ~done] = np.nan
+    return f, lam, used
+
+
+def boltzmann_h(f: np.ndarray, lat: Lattice | None = None):
+    """H = <f, log(f/w) - 1> (Sec. III) per site; f[81, ...] positive."""
+    lat = lat or velocity_set()
+    w = lat.w.reshape((lat.q,) + (1,) * (np.ndim(f) - 1))
+    return (f * (np.log(f / w) - 1.0)).sum(axis=0)
 
 
 # ---------------------------------------------------------------------------------------
