@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=512, help="TGV grid edge of the headline workload")
     p.add_argument("--storage", default="f32", choices=sorted(BYTES))
+    p.add_argument("--equilibrium", default="series", choices=["series", "entropic"],
+                   help="for --quick runs: the equilibrium of the timed case")
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--served-only", type=int, default=0, metavar="N",
@@ -222,12 +224,13 @@ def time_steps(B, ctx, stream, steps: int, warmup: int, world: int, sampler=None
     return ms, B.lbm_launch_count(ctx) - launches0, clocks
 
 
-def run_case(B, n: int, storage: str, steps: int, warmup: int, world: int, fp64_moments=False, sampler=None):
+def run_case(B, n: int, storage: str, steps: int, warmup: int, world: int, fp64_moments=False, sampler=None,
+             eq="series"):
     """Creates a TGV n^3 context, times `steps` steps; returns a dict of measurements."""
     import torch
     from paper_2409_05114_gb300 import workloads as W
     stream = torch.cuda.Stream()
-    cfg = B.make_config(n, n, n, 0.51 - 0.5, storage, fp64_moments=fp64_moments, stream=stream)
+    cfg = B.make_config(n, n, n, 0.51 - 0.5, storage, fp64_moments=fp64_moments, stream=stream, equilibrium=eq)
     ctx = B.lbm_create(cfg)
     try:
         rho, u, th = tgv_fields_device(n)
@@ -392,7 +395,7 @@ def ours(args):
 
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(gpu_index_for_smi(local))
-    head = run_case(B, args.n, args.storage, args.steps, args.warmup, world, sampler=sampler)
+    head = run_case(B, args.n, args.storage, args.steps, args.warmup, world, sampler=sampler, eq=args.equilibrium)
     value = head["mlups"] * world
     achieved = head["gbs"]
     line = {
@@ -413,12 +416,17 @@ def ours(args):
     }
     if not args.quick and rank == 0:
         variants = {}
-        for name, n, st, mom in (("tgv128_f32", 128, "f32", False), ("tgv128_f64", 128, "f64", False),
-                                 ("tgv512_f16", 512, "f16", False), ("tgv512_bf16", 512, "bf16", False),
-                                 ("tgv512_f32_fp64moments", 512, "f32", True)):
-            if n == args.n and st == args.storage and not mom:
+        for name, n, st, mom, eq in (("tgv128_f32", 128, "f32", False, "series"),
+                                     ("tgv128_f64", 128, "f64", False, "series"),
+                                     ("tgv512_f16", 512, "f16", False, "series"),
+                                     ("tgv512_bf16", 512, "bf16", False, "series"),
+                                     ("tgv512_f32_fp64moments", 512, "f32", True, "series"),
+                                     ("tgv512_f32_entropic", 512, "f32", False, "entropic"),
+                                     ("tgv512_f16_entropic", 512, "f16", False, "entropic"),
+                                     ("tgv64_f64_entropic", 64, "f64", False, "entropic")):
+            if n == args.n and st == args.storage and not mom and eq == "series":
                 continue
-            r = run_case(B, n, st, max(5, args.steps // 2), 3, 1, fp64_moments=mom)
+            r = run_case(B, n, st, max(5, args.steps // 2), 3, 1, fp64_moments=mom, eq=eq)
             variants[name] = {"mlups": round(r["mlups"], 1), "gbs": round(r["gbs"], 1),
                               "roofline_frac": round(r["gbs"] / peak, 4), "ms_per_step": round(r["ms_per_step"], 4)}
         line["variants"] = variants

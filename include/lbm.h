@@ -75,6 +75,13 @@ typedef enum {
   LBM_BF16_OFFSET = 3 /* stored as BF16 offsets d_i = f_i / w_i - 1, collide in FP32 */
 } lbm_storage;
 
+typedef enum {
+  LBM_EQ_SERIES = 0,  /* the series form of App. B (temperature weights to eta^4, f^(2), f^(3), R-bar) */
+  LBM_EQ_ENTROPIC = 1 /* the exact entropic equilibrium of Sec. III: w_i rho exp(mu + zeta.c_i + gamma c_i^2)
+                         minimising H = <f, log(f/w) - 1>, its multipliers found per site by Newton on
+                         the paper's 5x5 moment system (positive populations; the Mach-2 regime) */
+} lbm_equilibrium;
+
 typedef struct {
   int kind;                          /* lbm_bc_kind */
   double rho, ux, uy, uz, theta;     /* state of an LBM_BC_EQ_INFLOW face; ignored otherwise */
@@ -92,6 +99,9 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
                          creates its own stream (which synchronises with the legacy
                          default stream) */
+  int equilibrium;    /* lbm_equilibrium (init, inflow faces and every step).  LBM_EQ_ENTROPIC
+                         needs fp64_moments = 0; a site whose Newton iteration breaks down
+                         raises the instability flag (LBM_EUNSTABLE) */
 } lbm_config;
 
 /* Device bytes lbm_create would allocate for this configuration (both population buffers
@@ -201,8 +211,8 @@ typedef struct {
  * population memory (the server adds ~170 MB of staging of its own); 1 <= max_cases <= 1024. */
 lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server** out);
 
-/* Queues one case: configuration (storage FP32, FP16 or BF16 offsets, fp64_moments = 0;
- * cuda_stream is ignored), initial fields in host memory (layout as lbm_init; copied
+/* Queues one case: configuration (storage FP32, FP16 or BF16 offsets, fp64_moments = 0,
+ * the series equilibrium; cuda_stream is ignored), initial fields in host memory (layout as lbm_init; copied
  * before the call returns) and nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case
  * alone exceeds the budget, LBM_EINVAL for an invalid configuration. */
 lbm_status lbm_submit(lbm_server* srv, const lbm_config* cfg, const double* rho, const double* u,

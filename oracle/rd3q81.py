@@ -434,11 +434,12 @@ def collide(f: np.ndarray, feq: np.ndarray, tau: float) -> np.ndarray:
 # ---------------------------------------------------------------------------------------
 
 def init(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None = None,
-         chunk: int = 1024):
+         chunk: int = 1024, eq: str = "series"):
     """Populations f[s, i, z, y, x] = feq(rho, u, theta) at every site of both sublattices.
 
     rho, theta: [2, nz, ny, nx]; u: [3, 2, nz, ny, nx]."""
     lat = lat or velocity_set()
+    eqf = _equilibrium_of(eq)
     rho = np.asarray(rho, dtype=np.float64)
     S = rho.shape
     r1 = rho.reshape(-1)
@@ -447,45 +448,56 @@ def init(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None 
     out = np.empty((lat.q, r1.size))
     for a in range(0, r1.size, chunk):
         b = min(a + chunk, r1.size)
-        out[:, a:b] = equilibrium(r1[a:b], u1[:, a:b], t1[a:b], lat)
+        out[:, a:b] = eqf(r1[a:b], u1[:, a:b], t1[a:b], lat)
     return np.moveaxis(out.reshape((lat.q,) + S), 0, 1).copy()
 
 
-def bc_feq(bc_spec, lat: Lattice | None = None):
+def bc_feq(bc_spec, lat: Lattice | None = None, eq: str = "series"):
     """81 inflow populations of an "eq_inflow" face spec ("eq_inflow", rho, ux, uy, uz, theta),
     else None."""
     if bc_spec[0] != "eq_inflow":
         return None
     _, r, ux, uy, uz, t = bc_spec
-    return equilibrium(np.array([r]), np.array([[ux], [uy], [uz]]), np.array([t]), lat)[:, 0]
+    return _equilibrium_of(eq)(np.array([r]), np.array([[ux], [uy], [uz]]), np.array([t]), lat)[:, 0]
+
+
+def _equilibrium_of(kind: str):
+    if kind == "series":
+        return equilibrium
+    if kind == "entropic":
+        return lambda rho, u, theta, lat=None: entropic_equilibrium(rho, u, theta, lat)[0].reshape(
+            (81,) + np.shape(rho))
+    raise ValueError(kind)
 
 
 def step(f: np.ndarray, tau: float, bc_x=(("periodic",), ("periodic",)),
-         lat: Lattice | None = None, chunk: int = 1024) -> np.ndarray:
+         lat: Lattice | None = None, chunk: int = 1024, eq: str = "series") -> np.ndarray:
     """One time step: boundary fill, pull streaming, moments, equilibrium, BGK collision.
 
     ``bc_x`` holds the -x and +x face specs: ("periodic",), ("zero_gradient",) or
-    ("eq_inflow", rho, ux, uy, uz, theta)."""
+    ("eq_inflow", rho, ux, uy, uz, theta).  ``eq`` selects the equilibrium: "series" (App. B)
+    or "entropic" (the exact minimiser of Sec. III)."""
     lat = lat or velocity_set()
+    eqf = _equilibrium_of(eq)
     kinds = (bc_x[0][0], bc_x[1][0])
     if (kinds[0] == "periodic") != (kinds[1] == "periodic"):
         raise ValueError("a periodic x face must be paired with a periodic x face")
-    feq_in = (bc_feq(bc_x[0], lat), bc_feq(bc_x[1], lat))
+    feq_in = (bc_feq(bc_x[0], lat, eq), bc_feq(bc_x[1], lat, eq))
     pre = stream(f, kinds, feq_in, lat)
     flat = np.moveaxis(pre, 1, 0).reshape(lat.q, -1)     # [81, sites]
     post = np.empty_like(flat)
     for a in range(0, flat.shape[1], chunk):
         b = min(a + chunk, flat.shape[1])
         rho, u, theta = moments(flat[:, a:b], lat)
-        feq = equilibrium(rho, u, theta, lat)
+        feq = eqf(rho, u, theta, lat)
         post[:, a:b] = collide(flat[:, a:b], feq, tau)
     return np.moveaxis(post.reshape((lat.q,) + f.shape[:1] + f.shape[2:]), 0, 1).copy()
 
 
 def run(f: np.ndarray, tau: float, nsteps: int, bc_x=(("periodic",), ("periodic",)),
-        lat: Lattice | None = None) -> np.ndarray:
+        lat: Lattice | None = None, eq: str = "series") -> np.ndarray:
     for _ in range(nsteps):
-        f = step(f, tau, bc_x, lat)
+        f = step(f, tau, bc_x, lat, eq=eq)
     return f
 
 

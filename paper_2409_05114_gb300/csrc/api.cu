@@ -41,6 +41,10 @@ lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
   if (!(std::isfinite(cfg->tau) && cfg->tau >= 0.0)) return *why = "tau must be finite and >= 0", LBM_EINVAL;
   if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return *why = "unknown storage", LBM_EINVAL;
   if (cfg->fp64_moments != 0 && cfg->fp64_moments != 1) return *why = "fp64_moments must be 0 or 1", LBM_EINVAL;
+  if (cfg->equilibrium != LBM_EQ_SERIES && cfg->equilibrium != LBM_EQ_ENTROPIC)
+    return *why = "equilibrium must be LBM_EQ_SERIES or LBM_EQ_ENTROPIC", LBM_EINVAL;
+  if (cfg->equilibrium == LBM_EQ_ENTROPIC && cfg->fp64_moments)
+    return *why = "the entropic equilibrium uses the storage's own moment arithmetic (fp64_moments = 0)", LBM_EINVAL;
   for (int f = 0; f < 6; ++f) {
     const lbm_bc& b = cfg->face[f];
     if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
@@ -201,7 +205,12 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     const lbm_bc& b = cfg->face[face];
     ctx->zero_grad[face] = b.kind == LBM_BC_ZERO_GRADIENT;
     ctx->inflow[face] = b.kind == LBM_BC_EQ_INFLOW;
-    if (ctx->inflow[face]) lbm::equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
+    if (ctx->inflow[face]) {
+      if (cfg->equilibrium == LBM_EQ_ENTROPIC)
+        lbm::entropic_all<double>(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
+      else
+        lbm::equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
+    }
   }
 
   auto bail = [&](lbm_status st, const std::string& msg) {
@@ -246,8 +255,10 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
   DeviceGuard dg(ctx->device);
   const long long S = ctx->sites;
   ctx->cur = 0;
+  LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
   if (on_device) {
-    LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], rho, u, theta, 0, S, S, ctx->stream));
+    LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], rho, u, theta, 0,
+                                 S, S, ctx->stream, ctx->d_flag));
     ++ctx->launches;
   } else {
     double* sr = ctx->d_scratch;
@@ -260,14 +271,13 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
       for (int a = 0; a < 3; ++a)
         LBM_CK(ctx, cudaMemcpyAsync(su + a * cnt, u + a * S + first, nb, cudaMemcpyHostToDevice, ctx->stream));
       LBM_CK(ctx, cudaMemcpyAsync(st, theta + first, nb, cudaMemcpyHostToDevice, ctx->stream));
-      LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], sr, su, st, first, cnt, cnt,
-                                   ctx->stream));
+      LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], sr, su, st,
+                                   first, cnt, cnt, ctx->stream, ctx->d_flag));
       ++ctx->launches;
     }
   }
   lbm_status st = fill_inflow_faces(ctx);
   if (st != LBM_OK) return st;
-  LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
   if (!on_device) LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->initialized = true;
   return LBM_OK;
@@ -290,7 +300,7 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, cudaStream_t s) {
   p.src = ctx->buf[cur];
   p.dst = ctx->buf[cur ^ 1];
   lbm::fill_slab_bases(&p, ctx->elem);
-  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, p, s);
+  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, ctx->cfg.equilibrium, p, s);
 }
 
 int launches_per_step(const lbm_ctx* ctx) { return 1 + (ctx->zero_grad[0] ? 1 : 0) + (ctx->zero_grad[1] ? 1 : 0); }

@@ -36,9 +36,10 @@ __device__ __forceinline__ void encode(S* p, double f, double w) {
   }
 }
 
-template <class S>
+template <class S, int kEq>
 __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double* rho, const double* u,
-                            const double* theta, long long first, long long count, long long us) {
+                            const double* theta, long long first, long long count, long long us,
+                            unsigned int* flag) {
   const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
   if (k >= count) return;
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
@@ -49,7 +50,13 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
   // FP64 for FP64 populations, FP32 otherwise (offset storage directly as feq/w - 1).
   using R = typename Codec<S>::Real;
   R feq[kQ];
-  equilibrium_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab, feq);
+  if constexpr (kEq == 0) {
+    equilibrium_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab, feq);
+  } else {
+    if (!entropic_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab,
+                                            feq))
+      atomicOr(flag, 1u);
+  }
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     if constexpr (Codec<S>::kOffset)
@@ -247,12 +254,18 @@ unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kAuxBlock -
     default: return cudaErrorInvalidValue;             \
   }
 
-cudaError_t launch_init(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
+cudaError_t launch_init(int storage, int eq, const Geometry& g, const LatticeTables& tab, void* buf,
                         const double* rho, const double* u, const double* theta,
-                        long long first_site, long long count, long long u_stride, cudaStream_t s) {
+                        long long first_site, long long count, long long u_stride, cudaStream_t s,
+                        unsigned int* flag) {
   if (count <= 0) return cudaSuccess;
-  LBM_STORAGE_DISPATCH(storage, (init_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride)));
+  if (eq == 1) {
+    LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 1><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+  } else {
+    LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 0><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+  }
   return cudaGetLastError();
 }
 
@@ -321,12 +334,12 @@ cudaError_t launch_totals(int storage, const Geometry& g, const LatticeTables& t
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream_collide(int storage, int fp64_moments, const StepParams& p, cudaStream_t s) {
+cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, const StepParams& p, cudaStream_t s) {
   switch (storage) {
-    case kF64: return launch_sc_f64(fp64_moments, p, s);
-    case kF32: return launch_sc_f32(fp64_moments, p, s);
-    case kF16Off: return launch_sc_f16(fp64_moments, p, s);
-    case kBF16Off: return launch_sc_bf16(fp64_moments, p, s);
+    case kF64: return launch_sc_f64(fp64_moments, eq, p, s);
+    case kF32: return launch_sc_f32(fp64_moments, eq, p, s);
+    case kF16Off: return launch_sc_f16(fp64_moments, eq, p, s);
+    case kBF16Off: return launch_sc_bf16(fp64_moments, eq, p, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -2,6 +2,7 @@
 // evaluation, index wrapping, and the App. B equilibrium written once for any real type.
 #pragma once
 
+#include <cmath>
 #include <type_traits>
 #include <utility>
 
@@ -133,6 +134,157 @@ __host__ __device__ inline void equilibrium_all(R rho, R ux, R uy, R uz, R theta
 __host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy, double uz,
                                                 double theta, const LatticeTables& tab, double* feq) {
   equilibrium_all<double, false>(rho, ux, uy, uz, theta, tab, feq);
+}
+
+// ---- exact entropic equilibrium (Sec. III) --------------------------------------------
+// f_i = w_i rho exp(mu + zeta.c_i + gamma c_i^2), the minimiser of H = <f, log(f/w) - 1> at the
+// given conserved moments T = (rho, j_x, j_y, j_z, <f, c^2>).  The multipliers
+// lam = (mu, zeta_x, zeta_y, zeta_z, gamma) follow the paper's iteration: evaluate f at the
+// current guess, form the 5x5 matrix <f, phi_a phi_b> and the residual T_a - <f, phi_a>
+// (phi = 1, c_x, c_y, c_z, c^2), solve for the correction (Cholesky), add it, repeat.  The
+// first guess is the continuous Maxwellian's multipliers relative to w ~ exp(-c^2/(2 theta0)).
+// Per shell s the factor e_s = rho w_s exp(mu + gamma c_s^2) is shared by all its members;
+// per +/- pair p, exp(+-zeta.c_p) gives both, so one evaluation takes 11 + 40 exponentials.
+
+template <class R>
+__host__ __device__ __forceinline__ R eexp(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return exp(x); else return expf(x);
+}
+template <class R>
+__host__ __device__ __forceinline__ R elog(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return log(x); else return logf(x);
+}
+template <class R>
+__host__ __device__ __forceinline__ R esqrt(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return sqrt(x); else return sqrtf(x);
+}
+
+// zeta . c for the +c member of pair P.
+template <int P, class R>
+__host__ __device__ __forceinline__ R zeta_dot_c(const R* lam) {
+  constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+  R x = R(0);
+  if constexpr (d.hx != 0) x += R(0.5 * d.hx) * lam[1];
+  if constexpr (d.hy != 0) x += R(0.5 * d.hy) * lam[2];
+  if constexpr (d.hz != 0) x += R(0.5 * d.hz) * lam[3];
+  return x;
+}
+
+// Shell factors e_s = rho * ws_s * exp(mu + gamma c_s^2), ws = w (kOverW false) or 1.
+template <class R, bool kOverW>
+__host__ __device__ __forceinline__ void entropic_shell_factors(const R* lam, R rho, const LatticeTables& tb, R* e) {
+  const bool dbl = sizeof(R) == sizeof(double);
+  static_for<kShells>([&](auto Sc) {
+    constexpr int s = decltype(Sc)::value;
+    constexpr double c2 = rd3q81::kShellC2[s];
+    const R ws = kOverW ? R(1) : (dbl ? R(tb.w[s]) : R(tb.wf[s]));
+    e[s] = rho * ws * eexp(lam[0] + lam[4] * R(c2));
+  });
+}
+
+// Solves the symmetric positive definite 5x5 system J x = r in place (Cholesky); J is given
+// by its 15 distinct entries in the order 00 01 02 03 04 11 12 13 14 22 23 24 33 34 44.
+template <class R>
+__host__ __device__ __forceinline__ bool solve_spd5(const R* Jp, R* x) {
+  R a[5][5];
+  int k = 0;
+  for (int i = 0; i < 5; ++i)
+    for (int j = i; j < 5; ++j) a[i][j] = a[j][i] = Jp[k++];
+  R Lm[5][5];
+  for (int j = 0; j < 5; ++j) {
+    R d = a[j][j];
+    for (int m = 0; m < j; ++m) d -= Lm[j][m] * Lm[j][m];
+    if (!(d > R(0))) return false;
+    const R ljj = esqrt(d);
+    const R il = R(1) / ljj;
+    Lm[j][j] = ljj;
+    for (int i = j + 1; i < 5; ++i) {
+      R v = a[i][j];
+      for (int m = 0; m < j; ++m) v -= Lm[i][m] * Lm[j][m];
+      Lm[i][j] = v * il;
+    }
+  }
+  for (int i = 0; i < 5; ++i) {
+    R v = x[i];
+    for (int m = 0; m < i; ++m) v -= Lm[i][m] * x[m];
+    x[i] = v / Lm[i][i];
+  }
+  for (int i = 4; i >= 0; --i) {
+    R v = x[i];
+    for (int m = i + 1; m < 5; ++m) v -= Lm[m][i] * x[m];
+    x[i] = v / Lm[i][i];
+  }
+  return true;
+}
+
+// Newton for the multipliers.  T = conserved moments, (ux, uy, uz, theta) for the first guess.
+// On return lam holds the multipliers and e the shell factors of the last evaluation, whose
+// moments are within tol of T (or the best reached in max_it evaluations).  Returns false if
+// the iteration broke down (non-positive pivot or non-finite values).
+template <class R>
+__host__ __device__ __forceinline__ bool entropic_multipliers(const R* T, R ux, R uy, R uz, R theta, R tol,
+                                                              int max_it, const LatticeTables& tb, R* lam, R* e) {
+  const R q = ux * ux + uy * uy + uz * uz;
+  const R t0 = R(rd3q81::kTheta0);
+  lam[0] = R(-1.5) * elog(theta / t0) - q / (R(2) * theta);
+  lam[1] = ux / theta;
+  lam[2] = uy / theta;
+  lam[3] = uz / theta;
+  lam[4] = R(0.5) / t0 - R(0.5) / theta;
+  const R rho = T[0];
+  for (int it = 0;; ++it) {
+    entropic_shell_factors<R, false>(lam, rho, tb, e);
+    R J[15];
+    for (int k = 0; k < 15; ++k) J[k] = R(0);
+    J[0] = e[0];
+    static_for<kPairs>([&](auto Pc) {
+      constexpr int P = decltype(Pc)::value;
+      constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+      constexpr double c2 = rd3q81::kShellC2[d.shell];
+      constexpr double cx = 0.5 * d.hx, cy = 0.5 * d.hy, cz = 0.5 * d.hz;
+      const R a = eexp(zeta_dot_c<P, R>(lam));
+      const R ai = R(1) / a;
+      const R S = e[d.shell] * (a + ai), D = e[d.shell] * (a - ai);
+      J[0] += S;
+      J[4] += R(c2) * S;
+      J[14] += R(c2 * c2) * S;
+      if constexpr (cx != 0) { J[1] += R(cx) * D; J[5] += R(cx * cx) * S; J[8] += R(c2 * cx) * D; }
+      if constexpr (cy != 0) { J[2] += R(cy) * D; J[9] += R(cy * cy) * S; J[11] += R(c2 * cy) * D; }
+      if constexpr (cz != 0) { J[3] += R(cz) * D; J[12] += R(cz * cz) * S; J[13] += R(c2 * cz) * D; }
+      if constexpr (cx != 0 && cy != 0) J[6] += R(cx * cy) * S;
+      if constexpr (cx != 0 && cz != 0) J[7] += R(cx * cz) * S;
+      if constexpr (cy != 0 && cz != 0) J[10] += R(cy * cz) * S;
+    });
+    // J entries 02.. mirror: <f,c_x> = J01, <f,c_y> = J02, <f,c_z> = J03, <f,c^2> = J04,
+    // <f,c_x c^2> = J14 (index 8), etc.
+    R r[5] = {T[0] - J[0], T[1] - J[1], T[2] - J[2], T[3] - J[3], T[4] - J[4]};
+    const bool small = fabs(r[0]) <= tol * T[0] && fabs(r[1]) <= tol * T[0] && fabs(r[2]) <= tol * T[0] &&
+                       fabs(r[3]) <= tol * T[0] && fabs(r[4]) <= tol * T[4];
+    if (small || it + 1 >= max_it) return small || (J[0] == J[0]);
+    if (!solve_spd5<R>(J, r)) return false;
+    for (int k = 0; k < 5; ++k) lam[k] += r[k];
+  }
+}
+
+// Full exact entropic equilibrium of one state (feq_i, or feq_i / w_i with kOverW), or false
+// if the iteration broke down.
+template <class R, bool kOverW = false>
+__host__ __device__ inline bool entropic_all(R rho, R ux, R uy, R uz, R theta, const LatticeTables& tab, R* feq) {
+  constexpr bool kDbl = sizeof(R) == sizeof(double);
+  const R T[5] = {rho, rho * ux, rho * uy, rho * uz, rho * (ux * ux + uy * uy + uz * uz) + R(3) * rho * theta};
+  R lam[5], e[kShells];
+  const bool ok = entropic_multipliers<R>(T, ux, uy, uz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tab, lam, e);
+  if constexpr (kOverW)
+    for (int s = 0; s < kShells; ++s) e[s] /= R(kDbl ? tab.w[s] : tab.wf[s]);
+  feq[0] = e[0];
+  static_for<kPairs>([&](auto Pc) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
+    const R a = eexp(zeta_dot_c<P, R>(lam));
+    feq[1 + 2 * P] = e[s] * a;
+    feq[2 + 2 * P] = e[s] / a;
+  });
+  return ok;
 }
 
 // Wrap an index displaced by at most kReach into [0, n).

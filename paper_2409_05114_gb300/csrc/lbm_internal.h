@@ -120,16 +120,18 @@ inline size_t storage_bytes(int s) { return s == kF64 ? 8 : s == kF32 ? 4 : 2; }
 // ---- launchers (each defined in the translation unit of its storage type) --------------
 // Fused pull-stream + moments + equilibrium + BGK over every interior site of both
 // sublattices.  fp64_moments selects FP64 moment sums and temperature recovery.
-cudaError_t launch_stream_collide(int storage, int fp64_moments, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_f64(int fp64_moments, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_f32(int fp64_moments, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_f16(int fp64_moments, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_bf16(int fp64_moments, const StepParams& p, cudaStream_t s);
+// eq: 0 = series equilibrium (App. B), 1 = exact entropic equilibrium (Sec. III).
+cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_f64(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_f32(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_f16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_bf16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 
 // Auxiliary kernels (aux_kernels.cu).
-cudaError_t launch_init(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
+cudaError_t launch_init(int storage, int eq, const Geometry& g, const LatticeTables& tab, void* buf,
                         const double* rho, const double* u, const double* theta,
-                        long long first_site, long long count, long long u_stride, cudaStream_t s);
+                        long long first_site, long long count, long long u_stride, cudaStream_t s,
+                        unsigned int* flag);
 struct Feq81 {
   double v[kQ];
 };

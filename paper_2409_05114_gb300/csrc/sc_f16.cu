@@ -1,10 +1,12 @@
 // Fused stream-collide instantiations for __half storage (one translation unit per storage
-// type so that they compile in parallel).
+// type so that they compile in parallel): series equilibrium with FP32 or FP64 moments, and
+// the exact entropic equilibrium.
 #include "stream_collide.cuh"
 
 namespace lbm {
 
-cudaError_t launch_sc_f16(int fp64_moments, const StepParams& p, cudaStream_t s) {
+cudaError_t launch_sc_f16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s) {
+  if (eq == kEqEntropic) return launch_sc<__half, false, kEqEntropic>(p, s);
   return fp64_moments ? launch_sc<__half, true>(p, s) : launch_sc<__half, false>(p, s);
 }
 

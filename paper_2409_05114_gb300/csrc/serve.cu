@@ -241,7 +241,8 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
     for (int a = 0; a < 3; ++a)
       SRV_CK(s, cudaMemcpyAsync(su + a * cnt, r->in.data() + S + a * S + first, nb, cudaMemcpyHostToDevice, s->admit));
     SRV_CK(s, cudaMemcpyAsync(st, r->in.data() + 4 * S + first, nb, cudaMemcpyHostToDevice, s->admit));
-    SRV_CK(s, launch_init(r->cfg.storage, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt, s->admit));
+    SRV_CK(s, launch_init(r->cfg.storage, kEqSeries, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt, s->admit,
+                          s->d_flags + slot));
     ++s->stats.kernel_launches;
   }
   for (int face = 0; face < 2; ++face) {
@@ -505,9 +506,9 @@ lbm_status lbm_submit(lbm_server* s, const lbm_config* cfg, const double* rho, c
     s->err = why;
     return LBM_EINVAL;
   }
-  if (cfg->storage == LBM_F64 || cfg->fp64_moments) {
+  if (cfg->storage == LBM_F64 || cfg->fp64_moments || cfg->equilibrium != LBM_EQ_SERIES) {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments";
+    s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments and the series equilibrium";
     return LBM_EINVAL;
   }
   auto r = std::make_shared<Request>();

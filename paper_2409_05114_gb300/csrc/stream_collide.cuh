@@ -80,6 +80,7 @@ __device__ __forceinline__ void for_each_source(const Geometry& g, const Store* 
 // Conserved moments of Eq. (conslaws) in arithmetic M.
 template <class M>
 struct Moments {
+  using value_type = M;
   M rho, jx, jy, jz, E;
 };
 
@@ -127,7 +128,9 @@ __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* 
 
 // Temperature recovery, equilibrium (App. B) and BGK relaxation of one site's populations
 // f (in place), given their moments.
-template <class Store, class M>
+enum Equilibrium { kEqSeries = 0, kEqEntropic = 1 };
+
+template <class Store, class M, int kEq = kEqSeries>
 __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const Moments<M>& mo, double omega,
                                            unsigned int* flag, const LatticeTables& tb) {
   using C = Codec<Store>;
@@ -139,15 +142,27 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   const R rh = R(mo.rho);
   const R theta = R(mtheta);
   if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(flag, 1u);
-  // ---- equilibrium scalars, App. B ------------------------------------------------------
-  const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
-  EqScalars<R> e;
-  eq_scalars<R>(R(mux), R(muy), R(muz), theta, eta, tab_na<R>(tb), tab_nb<R>(tb), e);
-  // W~_s / w_s for offset storage (the collide then works on d = f/w - 1), W~_s otherwise.
-  R W[kShells];
+  // ---- equilibrium: App. B series (kEqSeries) or the exact minimiser of Sec. III ---------
+  [[maybe_unused]] EqScalars<R> e;
+  [[maybe_unused]] R W[kShells];     // series: W~_s (or W~_s / w_s); entropic: e_s (or e_s / w_s)
+  [[maybe_unused]] R lam[5];
+  if constexpr (kEq == kEqSeries) {
+    const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
+    eq_scalars<R>(R(mux), R(muy), R(muz), theta, eta, tab_na<R>(tb), tab_nb<R>(tb), e);
 #pragma unroll
-  for (int s = 0; s < kShells; ++s)
-    W[s] = rh * poly4(C::kOffset ? tab_p<R>(tb, s) : tab_wp<R>(tb, s), eta);
+    for (int s = 0; s < kShells; ++s)
+      W[s] = rh * poly4(C::kOffset ? tab_p<R>(tb, s) : tab_wp<R>(tb, s), eta);
+  } else {
+    constexpr bool kDbl = std::is_same_v<R, double>;
+    const R T[5] = {rh, R(mo.jx), R(mo.jy), R(mo.jz), R(mo.E)};
+    if (!entropic_multipliers<R>(T, R(mux), R(muy), R(muz), theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam,
+                                 W))
+      atomicOr(flag, 1u);
+    if constexpr (C::kOffset) {
+#pragma unroll
+      for (int s = 0; s < kShells; ++s) W[s] /= tab_w<R>(tb, s);
+    }
+  }
 
   // ---- BGK collision, Eq. (discretelbm) -------------------------------------------------
   // f_i <- f_i + omega D_i with D_i = f~eq_i - f_i.  In exact arithmetic D has zero mass,
@@ -163,7 +178,9 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   const R om = R(omega);
   R d1 = R(0), dE = R(0), dx = R(0), dy = R(0), dz = R(0);
   {
-    R feq0 = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
+    R feq0;
+    if constexpr (kEq == kEqSeries) feq0 = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
+    else feq0 = W[0];
     if constexpr (C::kOffset) feq0 -= R(1);
     const R D0 = feq0 - f[0];
     if constexpr (kProject) d1 = D0;
@@ -173,11 +190,19 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     constexpr int P = decltype(Pc)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
     constexpr int s = d.shell;
-    R ev, od;
-    eq_pair_parts<P, R>(e, ev, od);
-    const R we = W[s] * ev;
-    const R wo = W[s] * od;
-    R fp = we + wo, fm = we - wo;
+    R fp, fm;
+    if constexpr (kEq == kEqSeries) {
+      R ev, od;
+      eq_pair_parts<P, R>(e, ev, od);
+      const R we = W[s] * ev;
+      const R wo = W[s] * od;
+      fp = we + wo;
+      fm = we - wo;
+    } else {
+      const R a = eexp(zeta_dot_c<P, R>(lam));
+      fp = W[s] * a;
+      fm = W[s] / a;
+    }
     if constexpr (C::kOffset) {
       fp -= R(1);
       fm -= R(1);
@@ -251,7 +276,7 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
 
 // The single-case form of site_update: the same phases, with the slab base addresses taken
 // from the kernel parameters instead of being computed per access.
-template <class Store, bool kF64Mom, int SUB>
+template <class Store, bool kF64Mom, int SUB, int kEq>
 __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
   using C = Codec<Store>;
   using R = typename C::Real;
@@ -267,7 +292,7 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
     f[i] = C::load(static_cast<const Store*>(p.src_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
   });
   const auto mo = site_moments<Store, kF64Mom>(f, p.tab);
-  site_relax<Store>(f, mo, p.omega, p.flag, p.tab);
+  site_relax<Store, typename decltype(mo)::value_type, kEq>(f, mo, p.omega, p.flag, p.tab);
   const int own = zs[4] + ys[4] + xs[4];
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
@@ -278,27 +303,30 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
 // 4 for FP32/FP16/BF16 storage with FP32 moments (<= 128 registers, 16 warps per SM), 3 for
 // FP32 with FP64 moments, and no bound for FP64 storage (its 81 doubles need ~250).
-template <class Store, bool kF64Mom>
+template <class Store, bool kF64Mom, int kEq>
 constexpr int sc_min_blocks() {
-  return std::is_same_v<Store, double> ? 1 : (kF64Mom && std::is_same_v<Store, float>) ? 3 : 4;
+  if constexpr (std::is_same_v<Store, double>) return 1;
+  else if constexpr (kEq == kEqEntropic || kF64Mom) return 3;
+  else return 4;
 }
 
-template <class Store, bool kF64Mom>
-__global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom>()) stream_collide_kernel(const StepParams p) {
+template <class Store, bool kF64Mom, int kEq>
+__global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom, kEq>())
+    stream_collide_kernel(const StepParams p) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const long long t = static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
   if (t >= n) return;
   if (blockIdx.y == 0)
-    site_update_slabs<Store, kF64Mom, 0>(p, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 0, kEq>(p, static_cast<int>(t));
   else
-    site_update_slabs<Store, kF64Mom, 1>(p, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 1, kEq>(p, static_cast<int>(t));
 }
 
-template <class Store, bool kF64Mom>
+template <class Store, bool kF64Mom, int kEq = kEqSeries>
 cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const dim3 grid(static_cast<unsigned>((n + kScBlock - 1) / kScBlock), 2);
-  stream_collide_kernel<Store, kF64Mom><<<grid, kScBlock, 0, s>>>(p);
+  stream_collide_kernel<Store, kF64Mom, kEq><<<grid, kScBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -31,16 +31,17 @@ def lib_perm():
     return np.array([idx[tuple(int(x) for x in v)] for v in h])
 
 
-def oracle_run(wl, steps: int, tau: float):
-    f = O.init(wl.rho, wl.u, wl.theta)
-    f = O.run(f, tau, steps, wl.oracle_bc_x())
+def oracle_run(wl, steps: int, tau: float, eq: str = "series"):
+    f = O.init(wl.rho, wl.u, wl.theta, eq=eq)
+    f = O.run(f, tau, steps, wl.oracle_bc_x(), eq=eq)
     return f
 
 
-def gpu_run(wl, steps: int, tau: float, storage: str, fp64_moments=False, populations=None):
+def gpu_run(wl, steps: int, tau: float, storage: str, fp64_moments=False, populations=None, eq="series",
+            check_stable=False):
     """Returns (f_lib[2, 81, z, y, x] in library order, rho, u, theta) after `steps`."""
     from paper_2409_05114_gb300 import binding as B
-    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, fp64_moments)
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, fp64_moments, equilibrium=eq)
     ctx = B.lbm_create(cfg)
     try:
         if populations is None:
@@ -50,6 +51,8 @@ def gpu_run(wl, steps: int, tau: float, storage: str, fp64_moments=False, popula
         else:
             B.lbm_set_populations(ctx, np.ascontiguousarray(populations).reshape(-1))
         B.lbm_step(ctx, steps)
+        if check_stable:
+            B.lbm_sync(ctx)
         S = wl.sites
         rho, u, th = np.zeros(S), np.zeros(3 * S), np.zeros(S)
         B.lbm_moments(ctx, rho, u, th)

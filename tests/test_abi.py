@@ -21,7 +21,8 @@ def B():
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)))
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)          # drop comments
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|int|const char\s*\*)\s*(lbm_[a-z_0-9]+)\s*\(", text, flags=re.M)))
 
 
 def test_exports_every_declared_symbol(B):

@@ -1,0 +1,91 @@
+"""GPU parity of the exact entropic equilibrium (Sec. III; config equilibrium =
+LBM_EQ_ENTROPIC) against the oracle's Newton solution, and the regime it exists for: states
+where the series equilibrium of App. B leaves its range within a few steps (Mach 2, strong
+shocks) run stably and match the exact Riemann solution.
+
+Tolerances: FP64 -- both sides converge Newton to round-off, so 1e-11 relative; FP32 -- the
+FP32 Newton stops at the FP32 residual floor (~1e-6 relative, then the conservation
+projection), so fields within 1e-5 after 20 steps as for the series path."""
+
+import numpy as np
+import pytest
+
+from parity_util import ensure_built, field_errors, gpu_run, lib_perm, oracle_run, population_error
+from oracle import rd3q81 as O
+from paper_2409_05114_gb300 import workloads as W
+from riemann_exact import sample
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    ensure_built()
+    from paper_2409_05114_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def perm(B):
+    return lib_perm()
+
+
+@pytest.fixture(scope="module")
+def wlib(B):
+    return B.lbm_velocities()[1]
+
+
+@pytest.mark.parametrize("dims,steps,mach", [((10, 8, 6), 0, 0.5), ((10, 8, 6), 4, 0.5), ((13, 3, 2), 3, 1.5)])
+def test_fp64_entropic_parity(B, perm, wlib, dims, steps, mach):
+    wl = W.smooth_random(*dims, seed=17, mach=mach, eta=0.15)
+    tau = 0.1
+    f_ref = oracle_run(wl, steps, tau, eq="entropic")[:, perm]
+    f, r, u, t = gpu_run(wl, steps, tau, "f64", eq="entropic", check_stable=True)
+    scale = max(1.0, float(np.max(np.abs(f_ref) / wlib.reshape(1, 81, 1, 1, 1))))
+    assert population_error(f_ref, f, wlib) <= 1e-11 * scale
+    er = field_errors(O.fields(oracle_run(wl, steps, tau, eq="entropic")), (r, u, t))
+    assert max(er) <= 1e-11, er
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 2e-3)])
+def test_entropic_storage_parity_tgv(B, storage, tol):
+    wl = W.taylor_green(16, mach=0.5)
+    tau = wl.paper_tau("lb")
+    ref = O.fields(oracle_run(wl, 20, tau, eq="entropic"))
+    _, r, u, t = gpu_run(wl, 20, tau, storage, eq="entropic", check_stable=True)
+    er = field_errors(ref, (r, u, t))
+    print("entropic %s TGV16 20 steps: rel err rho %.3g u %.3g theta %.3g" % (storage, *er))
+    assert max(er) <= tol, er
+
+
+def test_mach2_blob_runs_with_entropic_equilibrium(B):
+    """The Mach-2 blob with its isentropic vortex: unstable at step 1 with the series
+    equilibrium, stable with the exact one; FP32 GPU matches the FP64 oracle."""
+    wl = W.mach2_blob(64, 16, 4)
+    tau = wl.paper_tau("literal")
+    ref = O.fields(oracle_run(wl, 10, tau, eq="entropic"))
+    _, r, u, t = gpu_run(wl, 10, tau, "f32", eq="entropic", check_stable=True)
+    er = field_errors(ref, (r, u, t))
+    print("entropic f32 Mach-2 blob 10 steps: rel err rho %.3g u %.3g theta %.3g" % er)
+    assert max(er) <= 1e-4, er
+    # and it keeps running: 300 more steps flag nothing
+    _, r, u, t = gpu_run(wl, 300, tau, "f32", eq="entropic", check_stable=True)
+    assert np.all(np.isfinite(r)) and np.all(t > 0)
+
+
+def test_strong_sod_entropic_matches_riemann(B):
+    """The Sod tube under the tau_lb reading (omega = 1.67) blows up with the series
+    equilibrium within ~20 steps; with the exact equilibrium the FP32 GPU run follows the
+    exact Euler solution (gamma = 5/3)."""
+    nx, steps = 512, 100
+    wl = W.sod(nx=nx, ny=1, nz=1)
+    _, r, u, t = gpu_run(wl, steps, wl.paper_tau("lb"), "f32", eq="entropic", check_stable=True)
+    x = np.concatenate([np.arange(nx) + 0.0, np.arange(nx) + 0.5])
+    o = np.argsort(x)
+    x, R, U, P = x[o], r.reshape(-1)[o], u[0].reshape(-1)[o], (r * t).reshape(-1)[o]
+    re, ue, pe, info = sample((1.0, 0.0, W.THETA0), (0.125, 0.0, 0.1 * W.THETA0), 5.0 / 3.0, (x - nx / 2) / steps)
+    x_shock = x[np.where(R > 0.5 * (info["rho_star_right"] + 0.125))[0].max()]
+    assert abs(x_shock - (nx / 2 + info["s_shock"] * steps)) < 3.0
+    plateau = (x > nx / 2 + info["s_tail"] * steps + 8) & (x < nx / 2 + info["s_shock"] * steps - 8)
+    assert abs(U[plateau].mean() / info["u_star"] - 1) < 0.02
+    assert abs(P[plateau].mean() / info["p_star"] - 1) < 0.02
