@@ -152,17 +152,18 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(storage: str, sites: int):
+def ncu_traffic(storage: str, sites: int, eq: str = "series"):
     """DRAM bytes (read + write) of one fused-kernel launch, from the committed ncu record
-    (bytes per site measured on a smaller grid, scaled by the sites); None if the record is
-    missing or the kernel sources changed since it was taken."""
+    (bytes per site measured on a smaller grid, scaled by the sites; keyed by storage, plus
+    "_entropic" for the exact-equilibrium kernel); None if the record is missing or the kernel
+    sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     if rec.get("source_sha256") != kernel_source_sha():
         return None
-    k = rec.get("kernels", {}).get(storage)
+    k = rec.get("kernels", {}).get(storage + ("_entropic" if eq == "entropic" else ""))
     return None if k is None else int(round(k["dram_bytes_per_site"] * sites))
 
 
@@ -408,7 +409,7 @@ def ours(args):
                    "streaming": "pull, ping-pong", "tau_lb": 0.51, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (one step moves %.0f GB)" % (head["bytes_per_site"] * head["sites"] / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"]),
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"], args.equilibrium),
                      "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                      "bytes_per_site": head["bytes_per_site"]},
         "gpu_launches": head["launches"],

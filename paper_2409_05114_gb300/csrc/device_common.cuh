@@ -143,8 +143,14 @@ __host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy
 // current guess, form the 5x5 matrix <f, phi_a phi_b> and the residual T_a - <f, phi_a>
 // (phi = 1, c_x, c_y, c_z, c^2), solve for the correction (Cholesky), add it, repeat.  The
 // first guess is the continuous Maxwellian's multipliers relative to w ~ exp(-c^2/(2 theta0)).
-// Per shell s the factor e_s = rho w_s exp(mu + gamma c_s^2) is shared by all its members;
-// per +/- pair p, exp(+-zeta.c_p) gives both, so one evaluation takes 11 + 40 exponentials.
+//
+// Evaluation.  With E_a = exp(zeta_a / 2) and c = h / 2, exp(zeta.c_i) = prod_a E_a^(h_ia).
+// The moving shells are walked in order of k, the common |h_a| of their members (1, 2, 3, 4,
+// 5, 6, 8), keeping P_a = E_a^k and Q_a = E_a^-k, so six exponentials serve all 80 moving
+// directions.  Over a whole shell the sums factor into C_a = P_a + Q_a and S_a = P_a - Q_a
+// (a BCC shell, for instance, has sum_i exp(zeta.c_i) = C_x C_y C_z), so the 15 moments cost a
+// few operations per shell; the shell factor rho w_s exp(mu + gamma c_s^2) adds one exponential
+// per shell.  The result is the same sum as the direction-by-direction one, regrouped.
 
 template <class R>
 __host__ __device__ __forceinline__ R eexp(R x) {
@@ -159,26 +165,122 @@ __host__ __device__ __forceinline__ R esqrt(R x) {
   if constexpr (sizeof(R) == sizeof(double)) return sqrt(x); else return sqrtf(x);
 }
 
-// zeta . c for the +c member of pair P.
-template <int P, class R>
-__host__ __device__ __forceinline__ R zeta_dot_c(const R* lam) {
-  constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
-  R x = R(0);
-  if constexpr (d.hx != 0) x += R(0.5 * d.hx) * lam[1];
-  if constexpr (d.hy != 0) x += R(0.5 * d.hy) * lam[2];
-  if constexpr (d.hz != 0) x += R(0.5 * d.hz) * lam[3];
-  return x;
+// Shell factor rho * ws * exp(mu + gamma c_s^2), ws = w_s (kOverW false) or 1.
+template <int s, bool kOverW, class R>
+__host__ __device__ __forceinline__ R entropic_shell_factor(const R* lam, R rho, const LatticeTables& tb) {
+  constexpr double c2 = rd3q81::kShellC2[s];
+  const R x = (s == 0) ? lam[0] : lam[0] + lam[4] * R(c2);
+  if constexpr (kOverW) {
+    return rho * eexp(x);
+  } else {
+    const R ws = sizeof(R) == sizeof(double) ? R(tb.w[s]) : R(tb.wf[s]);
+    return rho * ws * eexp(x);
+  }
 }
 
-// Shell factors e_s = rho * ws_s * exp(mu + gamma c_s^2), ws = w (kOverW false) or 1.
-template <class R, bool kOverW>
-__host__ __device__ __forceinline__ void entropic_shell_factors(const R* lam, R rho, const LatticeTables& tb, R* e) {
-  const bool dbl = sizeof(R) == sizeof(double);
-  static_for<kShells>([&](auto Sc) {
-    constexpr int s = decltype(Sc)::value;
-    constexpr double c2 = rd3q81::kShellC2[s];
-    const R ws = kOverW ? R(1) : (dbl ? R(tb.w[s]) : R(tb.wf[s]));
-    e[s] = rho * ws * eexp(lam[0] + lam[4] * R(c2));
+// Calls fn(std::integral_constant<int, K>, P, Q) for K = 1 .. kMaxShellK, with
+// P_a = E_a^K and Q_a = E_a^-K, E_a = exp(zeta_a / 2).
+template <class R, class F>
+__host__ __device__ __forceinline__ void axis_power_walk(const R* lam, F&& fn) {
+  R E[3], Ei[3], P[3], Q[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    E[a] = eexp(R(0.5) * lam[1 + a]);
+    Ei[a] = eexp(R(-0.5) * lam[1 + a]);
+    P[a] = E[a];
+    Q[a] = Ei[a];
+  }
+  static_for<rd3q81::kMaxShellK>([&](auto Kc) {
+    constexpr int K = decltype(Kc)::value + 1;
+    if constexpr (K > 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        P[a] *= E[a];
+        Q[a] *= Ei[a];
+      }
+    }
+    fn(std::integral_constant<int, K>{}, P, Q);
+  });
+}
+
+// The 15 distinct entries of <f, phi_a phi_b> (order 00 01 02 03 04 11 12 13 14 22 23 24 33 34
+// 44; <f, phi_a> = J[a] for a < 5) of f_i = w_i rho exp(lam . phi_i).
+template <class R>
+__host__ __device__ __forceinline__ void entropic_moment_matrix(const R* lam, R rho, const LatticeTables& tb, R* J) {
+#pragma unroll
+  for (int k = 0; k < 15; ++k) J[k] = R(0);
+  J[0] = entropic_shell_factor<0, false>(lam, rho, tb);
+  axis_power_walk<R>(lam, [&](auto Kc, const R* P, const R* Q) {
+    constexpr int K = decltype(Kc)::value;
+    static_for<kShells - 1>([&](auto Sc) {
+      constexpr int s = decltype(Sc)::value + 1;
+      constexpr rd3q81::ShellShape sh = rd3q81::shell_shape(s);
+      if constexpr (sh.k == K) {
+        constexpr double c2 = rd3q81::kShellC2[s];
+        constexpr double hk = 0.5 * K;
+        const R e = entropic_shell_factor<s, false>(lam, rho, tb);
+        const R C0 = P[0] + Q[0], C1 = P[1] + Q[1], C2 = P[2] + Q[2];
+        const R S0 = P[0] - Q[0], S1 = P[1] - Q[1], S2 = P[2] - Q[2];
+        // Z = sum exp(zeta.c), M_a = sum c_a exp / (k/2), N_ab = sum c_a c_b exp / (k/2)^2
+        R Z, M0, M1, M2, N0, N1, N2, X01 = R(0), X02 = R(0), X12 = R(0);
+        if constexpr (sh.kind == 1) {          // SC: (+-k, 0, 0) and permutations
+          Z = C0 + C1 + C2;
+          M0 = S0; M1 = S1; M2 = S2;
+          N0 = C0; N1 = C1; N2 = C2;
+        } else if constexpr (sh.kind == 2) {   // FCC: (+-k, +-k, 0) and permutations
+          const R Cs = C0 + C1 + C2;
+          Z = C0 * C1 + C0 * C2 + C1 * C2;
+          const R r0 = Cs - C0, r1 = Cs - C1, r2 = Cs - C2;
+          M0 = S0 * r0; M1 = S1 * r1; M2 = S2 * r2;
+          N0 = C0 * r0; N1 = C1 * r1; N2 = C2 * r2;
+          X01 = S0 * S1; X02 = S0 * S2; X12 = S1 * S2;
+        } else {                                // BCC: (+-k, +-k, +-k)
+          const R C12 = C1 * C2;
+          Z = C0 * C12;
+          M0 = S0 * C12; M1 = S1 * (C0 * C2); M2 = S2 * (C0 * C1);
+          N0 = Z; N1 = Z; N2 = Z;
+          X01 = S0 * S1 * C2; X02 = S0 * S2 * C1; X12 = S1 * S2 * C0;
+        }
+        const R eZ = e * Z, eh = e * R(hk), eh2 = e * R(hk * hk);
+        J[0] += eZ;
+        J[4] += R(c2) * eZ;
+        J[14] += R(c2 * c2) * eZ;
+        const R m0 = eh * M0, m1 = eh * M1, m2 = eh * M2;
+        J[1] += m0; J[2] += m1; J[3] += m2;
+        J[8] += R(c2) * m0; J[11] += R(c2) * m1; J[13] += R(c2) * m2;
+        J[5] += eh2 * N0; J[9] += eh2 * N1; J[12] += eh2 * N2;
+        if constexpr (sh.kind > 1) {
+          J[6] += eh2 * X01; J[7] += eh2 * X02; J[10] += eh2 * X12;
+        }
+      }
+    });
+  });
+}
+
+// Calls fn(pair constant P, v_plus, v_minus) for each +/- pair, with
+// v = rho ws exp(lam . phi) of its +c and -c members (ws = w, or 1 with kOverW), in the order
+// of the shell walk.  The rest value is entropic_shell_factor<0, kOverW>.
+template <class R, bool kOverW, class F>
+__host__ __device__ __forceinline__ void entropic_pair_values(const R* lam, R rho, const LatticeTables& tb, F&& fn) {
+  axis_power_walk<R>(lam, [&](auto Kc, const R* P, const R* Q) {
+    constexpr int K = decltype(Kc)::value;
+    [[maybe_unused]] R e = R(0);
+    static_for<kPairs>([&](auto Pc) {
+      constexpr int Pi = decltype(Pc)::value;
+      constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * Pi];
+      if constexpr (rd3q81::shell_shape(d.shell).k == K) {
+        if constexpr (Pi == 0 || rd3q81::kDirs[2 * Pi - 1].shell != d.shell)
+          e = entropic_shell_factor<d.shell, kOverW>(lam, rho, tb);
+        R vp = e, vm = e;
+        if constexpr (d.hx > 0) { vp *= P[0]; vm *= Q[0]; }
+        if constexpr (d.hx < 0) { vp *= Q[0]; vm *= P[0]; }
+        if constexpr (d.hy > 0) { vp *= P[1]; vm *= Q[1]; }
+        if constexpr (d.hy < 0) { vp *= Q[1]; vm *= P[1]; }
+        if constexpr (d.hz > 0) { vp *= P[2]; vm *= Q[2]; }
+        if constexpr (d.hz < 0) { vp *= Q[2]; vm *= P[2]; }
+        fn(Pc, vp, vm);
+      }
+    });
   });
 }
 
@@ -218,12 +320,12 @@ __host__ __device__ __forceinline__ bool solve_spd5(const R* Jp, R* x) {
 }
 
 // Newton for the multipliers.  T = conserved moments, (ux, uy, uz, theta) for the first guess.
-// On return lam holds the multipliers and e the shell factors of the last evaluation, whose
-// moments are within tol of T (or the best reached in max_it evaluations).  Returns false if
-// the iteration broke down (non-positive pivot or non-finite values).
+// On return lam holds multipliers whose moments are within tol of T (relative to rho for mass
+// and momentum, to <f, c^2> for energy), or the last iterate after max_it evaluations.
+// Returns false if the iteration broke down (non-positive pivot or non-finite values).
 template <class R>
 __host__ __device__ __forceinline__ bool entropic_multipliers(const R* T, R ux, R uy, R uz, R theta, R tol,
-                                                              int max_it, const LatticeTables& tb, R* lam, R* e) {
+                                                              int max_it, const LatticeTables& tb, R* lam) {
   const R q = ux * ux + uy * uy + uz * uz;
   const R t0 = R(rd3q81::kTheta0);
   lam[0] = R(-1.5) * elog(theta / t0) - q / (R(2) * theta);
@@ -233,30 +335,8 @@ __host__ __device__ __forceinline__ bool entropic_multipliers(const R* T, R ux, 
   lam[4] = R(0.5) / t0 - R(0.5) / theta;
   const R rho = T[0];
   for (int it = 0;; ++it) {
-    entropic_shell_factors<R, false>(lam, rho, tb, e);
     R J[15];
-    for (int k = 0; k < 15; ++k) J[k] = R(0);
-    J[0] = e[0];
-    static_for<kPairs>([&](auto Pc) {
-      constexpr int P = decltype(Pc)::value;
-      constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
-      constexpr double c2 = rd3q81::kShellC2[d.shell];
-      constexpr double cx = 0.5 * d.hx, cy = 0.5 * d.hy, cz = 0.5 * d.hz;
-      const R a = eexp(zeta_dot_c<P, R>(lam));
-      const R ai = R(1) / a;
-      const R S = e[d.shell] * (a + ai), D = e[d.shell] * (a - ai);
-      J[0] += S;
-      J[4] += R(c2) * S;
-      J[14] += R(c2 * c2) * S;
-      if constexpr (cx != 0) { J[1] += R(cx) * D; J[5] += R(cx * cx) * S; J[8] += R(c2 * cx) * D; }
-      if constexpr (cy != 0) { J[2] += R(cy) * D; J[9] += R(cy * cy) * S; J[11] += R(c2 * cy) * D; }
-      if constexpr (cz != 0) { J[3] += R(cz) * D; J[12] += R(cz * cz) * S; J[13] += R(c2 * cz) * D; }
-      if constexpr (cx != 0 && cy != 0) J[6] += R(cx * cy) * S;
-      if constexpr (cx != 0 && cz != 0) J[7] += R(cx * cz) * S;
-      if constexpr (cy != 0 && cz != 0) J[10] += R(cy * cz) * S;
-    });
-    // J entries 02.. mirror: <f,c_x> = J01, <f,c_y> = J02, <f,c_z> = J03, <f,c^2> = J04,
-    // <f,c_x c^2> = J14 (index 8), etc.
+    entropic_moment_matrix<R>(lam, rho, tb, J);
     R r[5] = {T[0] - J[0], T[1] - J[1], T[2] - J[2], T[3] - J[3], T[4] - J[4]};
     const bool small = fabs(r[0]) <= tol * T[0] && fabs(r[1]) <= tol * T[0] && fabs(r[2]) <= tol * T[0] &&
                        fabs(r[3]) <= tol * T[0] && fabs(r[4]) <= tol * T[4];
@@ -272,17 +352,13 @@ template <class R, bool kOverW = false>
 __host__ __device__ inline bool entropic_all(R rho, R ux, R uy, R uz, R theta, const LatticeTables& tab, R* feq) {
   constexpr bool kDbl = sizeof(R) == sizeof(double);
   const R T[5] = {rho, rho * ux, rho * uy, rho * uz, rho * (ux * ux + uy * uy + uz * uz) + R(3) * rho * theta};
-  R lam[5], e[kShells];
-  const bool ok = entropic_multipliers<R>(T, ux, uy, uz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tab, lam, e);
-  if constexpr (kOverW)
-    for (int s = 0; s < kShells; ++s) e[s] /= R(kDbl ? tab.w[s] : tab.wf[s]);
-  feq[0] = e[0];
-  static_for<kPairs>([&](auto Pc) {
+  R lam[5];
+  const bool ok = entropic_multipliers<R>(T, ux, uy, uz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tab, lam);
+  feq[0] = entropic_shell_factor<0, kOverW>(lam, rho, tab);
+  entropic_pair_values<R, kOverW>(lam, rho, tab, [&](auto Pc, R vp, R vm) {
     constexpr int P = decltype(Pc)::value;
-    constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
-    const R a = eexp(zeta_dot_c<P, R>(lam));
-    feq[1 + 2 * P] = e[s] * a;
-    feq[2 + 2 * P] = e[s] / a;
+    feq[1 + 2 * P] = vp;
+    feq[2 + 2 * P] = vm;
   });
   return ok;
 }

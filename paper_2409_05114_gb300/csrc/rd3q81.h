@@ -150,4 +150,38 @@ RD3Q81_HD constexpr int pull_disp(int h, int target_sub) {
 }
 RD3Q81_HD constexpr bool crosses_sublattice(const Dir& d) { return (d.hx % 2) != 0; }
 
+// Shape of a moving shell (s = 1..10): every member has |h_a| in {0, k} for each axis a, and
+// `kind` components are nonzero (1: SC, 2: FCC, 3: BCC), with all sign choices and axis
+// permutations present.  Sums of exp(zeta.c) over a shell therefore factor into per-axis
+// cosh / sinh of zeta_a k / 2.
+struct ShellShape {
+  int kind, k;
+};
+RD3Q81_HD constexpr int iabs(int a) { return a < 0 ? -a : a; }
+RD3Q81_HD constexpr ShellShape shell_shape(int s) {
+  for (int i = 1; i < kQ; ++i)
+    if (kDirs[i].shell == s) {
+      const int ax = iabs(kDirs[i].hx), ay = iabs(kDirs[i].hy), az = iabs(kDirs[i].hz);
+      const int k = ax > ay ? (ax > az ? ax : az) : (ay > az ? ay : az);
+      return {(ax != 0) + (ay != 0) + (az != 0), k};
+    }
+  return {0, 0};
+}
+constexpr int kMaxShellK = 8;  // SC-4
+RD3Q81_HD constexpr bool shells_are_uniform() {
+  for (int i = 1; i < kQ; ++i) {
+    const ShellShape sh = shell_shape(kDirs[i].shell);
+    const int h[3] = {kDirs[i].hx, kDirs[i].hy, kDirs[i].hz};
+    int nz = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (h[a] != 0 && iabs(h[a]) != sh.k) return false;
+      nz += h[a] != 0;
+    }
+    if (nz != sh.kind || sh.k > kMaxShellK || kShellCount[kDirs[i].shell] != (sh.kind == 2 ? 12 : sh.kind == 1 ? 6 : 8))
+      return false;
+  }
+  return true;
+}
+static_assert(shells_are_uniform(), "shell shapes");
+
 }  // namespace rd3q81

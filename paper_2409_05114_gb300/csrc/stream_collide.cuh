@@ -144,8 +144,8 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(flag, 1u);
   // ---- equilibrium: App. B series (kEqSeries) or the exact minimiser of Sec. III ---------
   [[maybe_unused]] EqScalars<R> e;
-  [[maybe_unused]] R W[kShells];     // series: W~_s (or W~_s / w_s); entropic: e_s (or e_s / w_s)
-  [[maybe_unused]] R lam[5];
+  [[maybe_unused]] R W[kShells];     // series: W~_s (or W~_s / w_s)
+  [[maybe_unused]] R lam[5];         // entropic: multipliers (mu, zeta, gamma)
   if constexpr (kEq == kEqSeries) {
     const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
     eq_scalars<R>(R(mux), R(muy), R(muz), theta, eta, tab_na<R>(tb), tab_nb<R>(tb), e);
@@ -155,13 +155,8 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   } else {
     constexpr bool kDbl = std::is_same_v<R, double>;
     const R T[5] = {rh, R(mo.jx), R(mo.jy), R(mo.jz), R(mo.E)};
-    if (!entropic_multipliers<R>(T, R(mux), R(muy), R(muz), theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam,
-                                 W))
+    if (!entropic_multipliers<R>(T, R(mux), R(muy), R(muz), theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam))
       atomicOr(flag, 1u);
-    if constexpr (C::kOffset) {
-#pragma unroll
-      for (int s = 0; s < kShells; ++s) W[s] /= tab_w<R>(tb, s);
-    }
   }
 
   // ---- BGK collision, Eq. (discretelbm) -------------------------------------------------
@@ -177,32 +172,15 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   constexpr bool kProject = std::is_same_v<Store, float>;
   const R om = R(omega);
   R d1 = R(0), dE = R(0), dx = R(0), dy = R(0), dz = R(0);
-  {
-    R feq0;
-    if constexpr (kEq == kEqSeries) feq0 = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
-    else feq0 = W[0];
+  auto relax_rest = [&](R feq0) {
     if constexpr (C::kOffset) feq0 -= R(1);
     const R D0 = feq0 - f[0];
-    if constexpr (kProject) d1 = D0;
+    if constexpr (kProject) d1 += D0;
     f[0] += om * D0;
-  }
-  static_for<kPairs>([&](auto Pc) {
+  };
+  auto relax_pair = [&](auto Pc, R fp, R fm) {
     constexpr int P = decltype(Pc)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
-    constexpr int s = d.shell;
-    R fp, fm;
-    if constexpr (kEq == kEqSeries) {
-      R ev, od;
-      eq_pair_parts<P, R>(e, ev, od);
-      const R we = W[s] * ev;
-      const R wo = W[s] * od;
-      fp = we + wo;
-      fm = we - wo;
-    } else {
-      const R a = eexp(zeta_dot_c<P, R>(lam));
-      fp = W[s] * a;
-      fm = W[s] / a;
-    }
     if constexpr (C::kOffset) {
       fp -= R(1);
       fm -= R(1);
@@ -210,7 +188,7 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     const R Dp = fp - f[1 + 2 * P];
     const R Dm = fm - f[2 + 2 * P];
     if constexpr (kProject) {
-      constexpr double c2 = rd3q81::kShellC2[s];
+      constexpr double c2 = rd3q81::kShellC2[d.shell];
       const R sD = Dp + Dm, dD = Dp - Dm;
       d1 += sD;
       dE += R(c2) * sD;
@@ -220,7 +198,23 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     }
     f[1 + 2 * P] += om * Dp;
     f[2 + 2 * P] += om * Dm;
-  });
+  };
+  if constexpr (kEq == kEqSeries) {
+    relax_rest(W[0] * (e.c0 + e.k0 * (R(0) - e.t3)));
+    static_for<kPairs>([&](auto Pc) {
+      constexpr int P = decltype(Pc)::value;
+      constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
+      R ev, od;
+      eq_pair_parts<P, R>(e, ev, od);
+      const R we = W[s] * ev;
+      const R wo = W[s] * od;
+      relax_pair(Pc, we + wo, we - wo);
+    });
+  } else {
+    // f~eq / w_i for offset storage: the weights cancel against the codec's 1 + d form.
+    relax_rest(entropic_shell_factor<0, C::kOffset>(lam, rh, tb));
+    entropic_pair_values<R, C::kOffset>(lam, rh, tb, relax_pair);
+  }
   if constexpr (kProject) {
     constexpr double t0 = rd3q81::kTheta0;
     const R g = (dE - R(3.0 * t0) * d1) * R(1.0 / (6.0 * t0 * t0));
@@ -306,7 +300,7 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 template <class Store, bool kF64Mom, int kEq>
 constexpr int sc_min_blocks() {
   if constexpr (std::is_same_v<Store, double>) return 1;
-  else if constexpr (kEq == kEqEntropic || kF64Mom) return 3;
+  else if constexpr (kF64Mom) return 3;
   else return 4;
 }
 
