@@ -25,8 +25,10 @@ read against the paper line by line:
                           step.  Half-integer links join the primary lattice (P, integer
                           positions) and the replica lattice (R, positions + (1/2,1/2,1/2)),
                           Sec. I (replica grid) and Sec. V (body-centred cubic lattice).
-* ``collide``             Sec. II, Eq. (discretelbm), right side: alpha = 2,
-                          beta = dt / (2 tau + dt) with dt = 1.
+* ``collide``             Sec. II, Eq. (discretelbm), right side: alpha = 2 (BGK) or the
+                          entropic alpha, beta = dt / (2 tau + dt) with dt = 1.
+* ``entropic_alpha``      Sec. II, Eq. (delH): the nontrivial root of
+                          H[f + alpha (feq - f)] - H[f] = 0 (``entropic_delta_h``).
 * ``fill_ghosts_x``       Boundary layers in x.  The paper names its own boundary
                           conditions without formulas; this oracle implements the three the
                           library offers (periodic, zero-gradient outflow, equilibrium
@@ -35,8 +37,10 @@ read against the paper line by line:
 Parity pins (tests/test_oracle_*.py): lattice identities in exact arithmetic, the paper's
 printed moment-error column, W~ against its closed-form generating function, equilibrium
 moments, uniform-state fixed points, conservation on periodic grids, cubic-symmetry
-equivariance, the closed-form sound speed and the exact Sod/Riemann solution.  No function
-here is "parity unpinned".
+equivariance, the closed-form sound speed and the exact Sod/Riemann solution; the entropic
+equilibrium's constraints, optimality conditions and small-velocity limit; Delta H against the
+definition of H in 50-digit arithmetic, the root's small-deviation limit alpha -> 2 + a3/(3 a2)
+and the discrete H theorem of whole steps.  No function here is "parity unpinned".
 
 Array conventions (all float64):
     populations  f[s, i, z, y, x]   s = 0 (P) or 1 (R), i = direction (this module's order)
@@ -424,9 +428,110 @@ def beta_of_tau(tau: float) -> float:
     return 1.0 / (2.0 * tau + 1.0)
 
 
-def collide(f: np.ndarray, feq: np.ndarray, tau: float) -> np.ndarray:
-    """f + alpha beta (feq - f) with alpha = 2 (Eq. (discretelbm))."""
-    return f + 2.0 * beta_of_tau(tau) * (feq - f)
+def collide(f: np.ndarray, feq: np.ndarray, tau: float, alpha=2.0) -> np.ndarray:
+    """f + alpha beta (feq - f) (Eq. (discretelbm)); alpha = 2 (BGK) or one value per site."""
+    return f + np.asarray(alpha) * beta_of_tau(tau) * (feq - f)
+
+
+def _phi(y):
+    """(1 + y) log(1 + y) - y for y >= -1 (its limit 1 at y = -1)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = (1.0 + y) * np.log1p(y) - y
+    return np.where(y <= -1.0, 1.0, v)
+
+
+def entropic_delta_h(alpha, f, feq):
+    """Delta H(alpha) = H[f + alpha (feq - f)] - H[f] of Eq. (delH), H = <f, log(f/w) - 1>,
+    for feq the exact entropic equilibrium of f's own conserved moments.
+
+    With D = feq - f and x = D / f: H[f + alpha D] - H[f] = <alpha D, log(f/w)> +
+    <f, (1 + alpha x) log(1 + alpha x) - alpha x>.  Because log(feq / w) = mu + zeta.c + gamma c^2
+    and D carries no mass, momentum or energy, <D, log(feq/w)> = 0, so
+    <D, log(f/w)> = -<D, log(feq/f)> = -<f, x log(1 + x)>, and
+
+        Delta H(alpha) = <f, (1 + alpha x) log(1 + alpha x) - alpha x> - alpha <f, x log(1 + x)>,
+
+    a sum of terms of order f x^2 with no cancellation between O(1) numbers.  f, feq [81, n]
+    (positive), alpha scalar or [n]."""
+    x = (feq - f) / f
+    b = (f * x * np.log1p(x)).sum(axis=0)
+    return (f * _phi(np.asarray(alpha) * x)).sum(axis=0) - np.asarray(alpha) * b
+
+
+def entropic_alpha(f, feq, max_iter: int = 200):
+    """Entropic alpha (Sec. II, Eq. (delH)): the nontrivial root alpha > 0 of
+    H[f + alpha (feq - f)] - H[f] = 0, per site, with feq the exact entropic equilibrium.
+
+    Along the line f + alpha D, Delta H is convex, zero at alpha = 0, falls at first (at alpha = 1
+    it is H[feq] - H[f] < 0), so it has exactly one positive root where it rises through zero,
+    provided the root lies where every population stays positive, alpha < alpha_max =
+    min over D_i < 0 of f_i / (-D_i).
+    * Newton from alpha = 2 when Delta H(2) > 0: for a convex function started right of its
+      root the iterates decrease monotonically to it.  Stops when a step is below 1e-15 alpha.
+    * otherwise the root lies above 2: bisection on [1, alpha_max] (or on [1, hi] with hi
+      doubled from 2 until Delta H(hi) > 0), 200 halvings.
+    * no sign change up to alpha_max: alpha = alpha_max (the furthest positive state on the line).
+    * f = feq (no deviation): alpha = 2, the limit of the root as D -> 0.
+    * some f_i <= 0 (H undefined): alpha = 2.
+    f, feq [81, n]; returns alpha [n]."""
+    f = np.asarray(f, dtype=np.float64)
+    feq = np.asarray(feq, dtype=np.float64)
+    n = f.shape[1]
+    alpha = np.full(n, 2.0)
+    pos = np.all(f > 0, axis=0)
+    D = feq - f
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x = np.where(pos, D / np.where(pos, f, 1.0), 0.0)
+        amax = np.where(x < 0, -1.0 / np.where(x < 0, x, -1.0), np.inf).min(axis=0)
+    b = (f * x * np.log1p(x)).sum(axis=0)
+    live = pos & (b > 0)
+    if not live.any():
+        return alpha
+
+    def F(a, k):
+        return (f[:, k] * _phi(a * x[:, k])).sum(axis=0) - a * b[k]
+
+    def dF(a, k):
+        return (f[:, k] * x[:, k] * np.log1p(a * x[:, k])).sum(axis=0) - b[k]
+
+    k_all = np.nonzero(live)[0]
+    newton = np.zeros(n, dtype=bool)
+    ok2 = amax[k_all] > 2.0
+    f2 = np.full(k_all.size, -1.0)
+    f2[ok2] = F(2.0, k_all[ok2])
+    newton[k_all[f2 > 0]] = True
+    # Newton from 2 (monotone from the right)
+    k = np.nonzero(newton)[0]
+    a = np.full(k.size, 2.0)
+    act = np.ones(k.size, dtype=bool)
+    for _ in range(max_iter):
+        if not act.any():
+            break
+        kk = k[act]
+        step = F(a[act], kk) / dF(a[act], kk)
+        a[act] -= step
+        act[act] = np.abs(step) > 1e-15 * a[act]
+    alpha[k] = a
+    # bisection above 2
+    k = k_all[~newton[k_all]]
+    if k.size:
+        lo = np.ones(k.size)
+        hi = np.where(np.isfinite(amax[k]), amax[k], 2.0)
+        grow = ~np.isfinite(amax[k])
+        for _ in range(60):
+            if not grow.any():
+                break
+            up = grow & (F(hi, k) <= 0)
+            hi = np.where(up, 2.0 * hi, hi)
+            grow = up
+        root = F(hi, k) > 0
+        for _ in range(max_iter):
+            mid = 0.5 * (lo + hi)
+            neg = F(mid, k) <= 0
+            lo = np.where(neg, mid, lo)
+            hi = np.where(neg, hi, mid)
+        alpha[k] = np.where(root, 0.5 * (lo + hi), np.where(np.isfinite(amax[k]), amax[k], 2.0))
+    return alpha
 
 
 # ---------------------------------------------------------------------------------------
@@ -471,13 +576,19 @@ def _equilibrium_of(kind: str):
 
 
 def step(f: np.ndarray, tau: float, bc_x=(("periodic",), ("periodic",)),
-         lat: Lattice | None = None, chunk: int = 1024, eq: str = "series") -> np.ndarray:
-    """One time step: boundary fill, pull streaming, moments, equilibrium, BGK collision.
+         lat: Lattice | None = None, chunk: int = 1024, eq: str = "series",
+         collision: str = "bgk") -> np.ndarray:
+    """One time step: boundary fill, pull streaming, moments, equilibrium, collision.
 
     ``bc_x`` holds the -x and +x face specs: ("periodic",), ("zero_gradient",) or
     ("eq_inflow", rho, ux, uy, uz, theta).  ``eq`` selects the equilibrium: "series" (App. B)
-    or "entropic" (the exact minimiser of Sec. III)."""
+    or "entropic" (the exact minimiser of Sec. III).  ``collision`` is "bgk" (alpha = 2) or
+    "entropic" (alpha the root of Eq. (delH) per site; needs eq="entropic")."""
     lat = lat or velocity_set()
+    if collision not in ("bgk", "entropic"):
+        raise ValueError(collision)
+    if collision == "entropic" and eq != "entropic":
+        raise ValueError("the entropic alpha is defined with the entropic equilibrium")
     eqf = _equilibrium_of(eq)
     kinds = (bc_x[0][0], bc_x[1][0])
     if (kinds[0] == "periodic") != (kinds[1] == "periodic"):
@@ -490,14 +601,15 @@ def step(f: np.ndarray, tau: float, bc_x=(("periodic",), ("periodic",)),
         b = min(a + chunk, flat.shape[1])
         rho, u, theta = moments(flat[:, a:b], lat)
         feq = eqf(rho, u, theta, lat)
-        post[:, a:b] = collide(flat[:, a:b], feq, tau)
+        alpha = entropic_alpha(flat[:, a:b], feq) if collision == "entropic" else 2.0
+        post[:, a:b] = collide(flat[:, a:b], feq, tau, alpha)
     return np.moveaxis(post.reshape((lat.q,) + f.shape[:1] + f.shape[2:]), 0, 1).copy()
 
 
 def run(f: np.ndarray, tau: float, nsteps: int, bc_x=(("periodic",), ("periodic",)),
-        lat: Lattice | None = None, eq: str = "series") -> np.ndarray:
+        lat: Lattice | None = None, eq: str = "series", collision: str = "bgk") -> np.ndarray:
     for _ in range(nsteps):
-        f = step(f, tau, bc_x, lat, eq=eq)
+        f = step(f, tau, bc_x, lat, eq=eq, collision=collision)
     return f
 
 
