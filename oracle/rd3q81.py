@@ -15,6 +15,8 @@ read against the paper line by line:
                           weights as quintic polynomials of theta0, w_0 = 1 - sum(others).
 * ``moments``             Sec. II, Eq. (conslaws): rho, rho*u, rho*u^2 + 3*rho*theta.
 * ``temperature_weights`` App. B, Eq. (zeroveleqseries): the eta^4 series W~_i(theta).
+* ``temperature_weights_exact`` App. B, Eq. (zeroveleq): W_i = w_i A G^(4 c_i^2) with G the root of
+                          theta'(G) = F2/(3 theta0 F0), Eq. (f0f2geqn).
 * ``equilibrium``         App. B, "Discrete equilibrium at nonzero velocity": f~eq with
                           f^(2), f^(3), R-bar and the tensor R-bar_{kappa alpha zeta eta},
                           the last two as explicit 81-term sums over W~/rho.
@@ -40,7 +42,8 @@ moments, uniform-state fixed points, conservation on periodic grids, cubic-symme
 equivariance, the closed-form sound speed and the exact Sod/Riemann solution; the entropic
 equilibrium's constraints, optimality conditions and small-velocity limit; Delta H against the
 definition of H in 50-digit arithmetic, the root's small-deviation limit alpha -> 2 + a3/(3 a2)
-and the discrete H theorem of whole steps.  No function here is "parity unpinned".
+and the discrete H theorem of whole steps; the exact W(theta) against the entropic equilibrium at
+rest and its eta^4 series.  No function here is "parity unpinned".
 
 Array conventions (all float64):
     populations  f[s, i, z, y, x]   s = 0 (P) or 1 (R), i = direction (this module's order)
@@ -178,6 +181,40 @@ def temperature_weights(rho: np.ndarray, theta: np.ndarray, lat: Lattice | None 
     return rho * w * poly
 
 
+def temperature_weights_exact(rho: np.ndarray, theta: np.ndarray, lat: Lattice | None = None,
+                              tol: float = 1e-12, max_iter: int = 100):
+    """Exact temperature-dependent weights of App. B, Eq. (zeroveleq):
+
+        W_i(theta) = w_i A G^(4 c_i^2),   A = 1 / F0(G),   theta' = theta/theta0 = F2(G) / (3 theta0 F0(G)),
+
+    F0(G) = <w, G^(4 c^2)>, F2(G) = <w, c^2 G^(4 c^2)> (Eq. (f0f2geqn)), i.e. the weights that
+    keep mass <W, 1> = 1 and energy <W, c^2> = 3 theta.  The paper solves the 1-D relation
+    theta'(G) for G "with any iterative solver"; here in the variable g = 4 ln G, so that
+    G^(4 c^2) = exp(g c^2) (no large powers): Newton on r(g) = F2/F0 - 3 theta, whose slope
+    <c^4> - <c^2>^2 under the normalised weights is positive (a variance), from the paper's
+    series multiplier g0 = 1/(2 theta0) - 1/(2 theta) (the sum of its gamma^(0) series), until a
+    step is below tol (1 + |g|).  Returns rho * W [81, ...]; NaN where it did not converge."""
+    lat = lat or velocity_set()
+    rho = np.asarray(rho, dtype=np.float64)
+    th = np.asarray(theta, dtype=np.float64)
+    S = th.shape
+    t1 = th.reshape(-1)
+    g = 0.5 / lat.theta0 - 0.5 / t1
+    w, c2 = lat.w[:, None], lat.c2[:, None]
+    done = np.zeros(t1.size, dtype=bool)
+    for _ in range(max_iter):
+        e = w * np.exp(g * c2)
+        F0, F2, F4 = e.sum(axis=0), (e * c2).sum(axis=0), (e * c2 * c2).sum(axis=0)
+        step = (F2 / F0 - 3.0 * t1) / (F4 / F0 - (F2 / F0) ** 2)
+        g = np.where(done, g, g - step)
+        done |= np.abs(step) <= tol * (1.0 + np.abs(g))      # quadratic: the error left is ~step^2
+        if done.all():
+            break
+    W = w * np.exp(g * c2) / (w * np.exp(g * c2)).sum(axis=0)
+    W[:, ~done] = np.nan
+    return (rho.reshape(-1) * W).reshape((lat.q,) + S) if rho.ndim else rho * W.reshape((lat.q,) + S)
+
+
 def rbar(theta: np.ndarray, lat: Lattice | None = None, Wn: np.ndarray | None = None) -> np.ndarray:
     """Rb = <W~/rho, c^4> / (15 theta^2) - 1 (App. B), as an explicit 81-term sum.
     ``Wn`` may pass W~/rho at these temperatures if the caller already has it."""
@@ -205,7 +242,8 @@ def rbar_tensor_contraction(theta: np.ndarray, u: np.ndarray, lat: Lattice | Non
     return G @ (Wn * xi * xi * xi) / th ** 2 - 3.0 * q * xi
 
 
-def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None = None):
+def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice | None = None,
+                weights: str = "series"):
     """Series entropic equilibrium f~eq_i(rho, u, theta) of App. B (nonzero velocity):
 
         f~eq_i = W~_i(theta) [1 + u.c_i/theta + f_i^(2) + f_i^(3)]
@@ -224,6 +262,8 @@ def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice 
         u_a u_b u_g c_k Delta_abgk         = 3 u^2 (u.c)
         u_a u_z u_e c_ix Rb_{x a z e}      = sum_j (W~_j/rho) (c_j.c_i) (c_j.u)^3 / theta^2
                                              - 3 u^2 (u.c_i)
+    ``weights`` = "exact" takes the exact W(theta) of Eq. (zeroveleq) in place of the eta^4
+    series W~ (in W~ itself and in both Rb).
     Inputs are arrays over sites (any shape S, u is [3, *S]); returns feq[81, *S].
     """
     lat = lat or velocity_set()
@@ -234,7 +274,12 @@ def equilibrium(rho: np.ndarray, u: np.ndarray, theta: np.ndarray, lat: Lattice 
     rho1, th = rho.reshape(-1), theta.reshape(-1)
     u1 = u.reshape(3, -1)
 
-    W = temperature_weights(rho1, th, lat)               # [81, n]
+    if weights == "series":
+        W = temperature_weights(rho1, th, lat)           # [81, n]
+    elif weights == "exact":
+        W = temperature_weights_exact(rho1, th, lat)
+    else:
+        raise ValueError(weights)
     q = (u1 ** 2).sum(axis=0)                             # u^2
     xi = lat.c @ u1                                       # u.c_i      [81, n]
     c2 = lat.c2[:, None]
@@ -569,6 +614,8 @@ def bc_feq(bc_spec, lat: Lattice | None = None, eq: str = "series"):
 def _equilibrium_of(kind: str):
     if kind == "series":
         return equilibrium
+    if kind == "series_exact_w":
+        return lambda rho, u, theta, lat=None: equilibrium(rho, u, theta, lat, weights="exact")
     if kind == "entropic":
         return lambda rho, u, theta, lat=None: entropic_equilibrium(rho, u, theta, lat)[0].reshape(
             (81,) + np.shape(rho))
