@@ -77,10 +77,20 @@ typedef enum {
 
 typedef enum {
   LBM_EQ_SERIES = 0,  /* the series form of App. B (temperature weights to eta^4, f^(2), f^(3), R-bar) */
-  LBM_EQ_ENTROPIC = 1 /* the exact entropic equilibrium of Sec. III: w_i rho exp(mu + zeta.c_i + gamma c_i^2)
-                         minimising H = <f, log(f/w) - 1>, its multipliers found per site by Newton on
-                         the paper's 5x5 moment system (positive populations; the Mach-2 regime) */
+  LBM_EQ_ENTROPIC = 1, /* the exact entropic equilibrium of Sec. III: w_i rho exp(mu + zeta.c_i + gamma c_i^2)
+                          minimising H = <f, log(f/w) - 1>, its multipliers found per site by Newton on
+                          the paper's 5x5 moment system (positive populations; the Mach-2 regime) */
+  LBM_EQ_SERIES_EXACT_W = 2 /* the series form of App. B with the exact temperature weights
+                               W_i(theta) = w_i A G^(4 c_i^2) of Eq. (zeroveleq) (G per site by a 1-D
+                               Newton on theta'(G) = F2 / (3 theta0 F0)) in place of the eta^4 series */
 } lbm_equilibrium;
+
+typedef enum {
+  LBM_COLLISION_BGK = 0,     /* f += alpha beta (feq - f) with alpha = 2 (Eq. (discretelbm)) */
+  LBM_COLLISION_ENTROPIC = 1 /* alpha per site: the nontrivial root of H[f + alpha (feq - f)] - H[f] = 0
+                                (Eq. (delH), H = <f, log(f/w) - 1>), kept where every population stays
+                                positive; needs LBM_EQ_ENTROPIC */
+} lbm_collision;
 
 typedef struct {
   int kind;                          /* lbm_bc_kind */
@@ -99,9 +109,12 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
                          creates its own stream (which synchronises with the legacy
                          default stream) */
-  int equilibrium;    /* lbm_equilibrium (init, inflow faces and every step).  LBM_EQ_ENTROPIC
-                         needs fp64_moments = 0; a site whose Newton iteration breaks down
-                         raises the instability flag (LBM_EUNSTABLE) */
+  int equilibrium;    /* lbm_equilibrium (init, inflow faces and every step).  fp64_moments = 1
+                         is available with LBM_EQ_SERIES only; a site whose Newton iteration
+                         breaks down raises the instability flag (LBM_EUNSTABLE) */
+  int collision;      /* lbm_collision.  LBM_COLLISION_ENTROPIC needs equilibrium =
+                         LBM_EQ_ENTROPIC.  A site with a population <= 0 (where H is not
+                         defined) takes alpha = 2. */
 } lbm_config;
 
 /* Device bytes lbm_create would allocate for this configuration (both population buffers

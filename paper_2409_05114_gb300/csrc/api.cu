@@ -41,10 +41,16 @@ lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
   if (!(std::isfinite(cfg->tau) && cfg->tau >= 0.0)) return *why = "tau must be finite and >= 0", LBM_EINVAL;
   if (cfg->storage < LBM_F64 || cfg->storage > LBM_BF16_OFFSET) return *why = "unknown storage", LBM_EINVAL;
   if (cfg->fp64_moments != 0 && cfg->fp64_moments != 1) return *why = "fp64_moments must be 0 or 1", LBM_EINVAL;
-  if (cfg->equilibrium != LBM_EQ_SERIES && cfg->equilibrium != LBM_EQ_ENTROPIC)
-    return *why = "equilibrium must be LBM_EQ_SERIES or LBM_EQ_ENTROPIC", LBM_EINVAL;
-  if (cfg->equilibrium == LBM_EQ_ENTROPIC && cfg->fp64_moments)
-    return *why = "the entropic equilibrium uses the storage's own moment arithmetic (fp64_moments = 0)", LBM_EINVAL;
+  if (cfg->equilibrium != LBM_EQ_SERIES && cfg->equilibrium != LBM_EQ_ENTROPIC &&
+      cfg->equilibrium != LBM_EQ_SERIES_EXACT_W)
+    return *why = "equilibrium must be LBM_EQ_SERIES, LBM_EQ_ENTROPIC or LBM_EQ_SERIES_EXACT_W", LBM_EINVAL;
+  if (cfg->equilibrium != LBM_EQ_SERIES && cfg->fp64_moments)
+    return *why = "fp64_moments is available with the series equilibrium (LBM_EQ_SERIES) only", LBM_EINVAL;
+  if (cfg->collision != LBM_COLLISION_BGK && cfg->collision != LBM_COLLISION_ENTROPIC)
+    return *why = "collision must be LBM_COLLISION_BGK or LBM_COLLISION_ENTROPIC", LBM_EINVAL;
+  if (cfg->collision == LBM_COLLISION_ENTROPIC && cfg->equilibrium != LBM_EQ_ENTROPIC)
+    return *why = "the entropic alpha is defined with the exact entropic equilibrium (equilibrium = LBM_EQ_ENTROPIC)",
+           LBM_EINVAL;
   for (int f = 0; f < 6; ++f) {
     const lbm_bc& b = cfg->face[f];
     if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
@@ -208,6 +214,8 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     if (ctx->inflow[face]) {
       if (cfg->equilibrium == LBM_EQ_ENTROPIC)
         lbm::entropic_all<double>(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
+      else if (cfg->equilibrium == LBM_EQ_SERIES_EXACT_W)
+        lbm::equilibrium_all<double, false, true>(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
       else
         lbm::equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
     }
@@ -300,7 +308,11 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, cudaStream_t s) {
   p.src = ctx->buf[cur];
   p.dst = ctx->buf[cur ^ 1];
   lbm::fill_slab_bases(&p, ctx->elem);
-  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, ctx->cfg.equilibrium, p, s);
+  const int mode = ctx->cfg.equilibrium == LBM_EQ_ENTROPIC
+                       ? (ctx->cfg.collision == LBM_COLLISION_ENTROPIC ? lbm::kEqEntropicAlpha : lbm::kEqEntropic)
+                   : ctx->cfg.equilibrium == LBM_EQ_SERIES_EXACT_W ? lbm::kEqSeriesExactW
+                                                                    : lbm::kEqSeries;
+  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, mode, p, s);
 }
 
 int launches_per_step(const lbm_ctx* ctx) { return 1 + (ctx->zero_grad[0] ? 1 : 0) + (ctx->zero_grad[1] ? 1 : 0); }

@@ -52,6 +52,10 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
   R feq[kQ];
   if constexpr (kEq == 0) {
     equilibrium_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab, feq);
+  } else if constexpr (kEq == 2) {
+    if (!equilibrium_all<R, Codec<S>::kOffset, true>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]),
+                                                     R(theta[k]), tab, feq))
+      atomicOr(flag, 1u);
   } else {
     if (!entropic_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab,
                                             feq))
@@ -261,6 +265,9 @@ cudaError_t launch_init(int storage, int eq, const Geometry& g, const LatticeTab
   if (count <= 0) return cudaSuccess;
   if (eq == 1) {
     LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 1><<<blocks_for(count), kAuxBlock, 0, s>>>(
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+  } else if (eq == 2) {
+    LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 2><<<blocks_for(count), kAuxBlock, 0, s>>>(
                                       g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
   } else {
     LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 0><<<blocks_for(count), kAuxBlock, 0, s>>>(

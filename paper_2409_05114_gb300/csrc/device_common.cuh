@@ -20,6 +20,20 @@ __host__ __device__ __forceinline__ void static_for(F&& f) {
   static_for_impl(f, std::make_integer_sequence<int, N>());
 }
 
+// exp, log and sqrt in the arithmetic R (float or double).
+template <class R>
+__host__ __device__ __forceinline__ R eexp(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return exp(x); else return expf(x);
+}
+template <class R>
+__host__ __device__ __forceinline__ R elog(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return log(x); else return logf(x);
+}
+template <class R>
+__host__ __device__ __forceinline__ R esqrt(R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return sqrt(x); else return sqrtf(x);
+}
+
 // sum_k c[k] eta^k, k = 0..4 (Horner).
 template <class R>
 __host__ __device__ __forceinline__ R poly4(const R* c, R eta) {
@@ -43,15 +57,16 @@ struct EqScalars {
   R t3;      // 3 theta
 };
 
+// An = <W/rho, c_x^4> - 3 <W/rho, c_x^2 c_y^2> and Bn = <W/rho, c_x^2 c_y^2> - theta^2 (so that
+// A = An / theta^2, B = Bn / theta^2 and Rb = A/5 + B).
 template <class R>
-__host__ __device__ __forceinline__ void eq_scalars(R ux, R uy, R uz, R theta, R eta, const R* na,
-                                                    const R* nb, EqScalars<R>& e) {
+__host__ __device__ __forceinline__ void eq_scalars_ab(R ux, R uy, R uz, R theta, R An, R Bn, EqScalars<R>& e) {
   const R q = ux * ux + uy * uy + uz * uz;
   const R ith = R(1) / theta;
   const R ith2 = ith * ith;
   const R ith3 = ith2 * ith;
-  const R A = poly4(na, eta) * ith2;
-  const R B = poly4(nb, eta) * ith2;
+  const R A = An * ith2;
+  const R B = Bn * ith2;
   const R Rb = R(0.2) * A + B;
   const R K = Rb / (R(2) + R(5) * Rb);
   e.ux = ux;
@@ -68,6 +83,84 @@ __host__ __device__ __forceinline__ void eq_scalars(R ux, R uy, R uz, R theta, R
   e.c1 = ith - R(0.5) * q * ith2 + (R(5) * q * Rb - R(3) * B * q) * ith2 * R(1.0 / 6.0);
   e.k1 = -R(5.0 / 6.0) * ith3 * K * q;
   e.t3 = R(3) * theta;
+}
+
+// With the eta^4 series W~: An, Bn are quartic polynomials in eta (coefficients na, nb).
+template <class R>
+__host__ __device__ __forceinline__ void eq_scalars(R ux, R uy, R uz, R theta, R eta, const R* na,
+                                                    const R* nb, EqScalars<R>& e) {
+  eq_scalars_ab<R>(ux, uy, uz, theta, poly4(na, eta), poly4(nb, eta), e);
+}
+
+// ---- exact temperature weights (App. B, Eq. (zeroveleq)) -----------------------------------
+// W_i(theta) = w_i A G^(4 c_i^2) with A = 1 / F0 and G fixed by theta' = F2 / (3 theta0 F0),
+// F0 = <w, G^(4 c^2)>, F2 = <w, c^2 G^(4 c^2)> (Eq. (f0f2geqn)).  In g = 4 ln G the powers are
+// exp(g c_s^2), one exponential per shell.  Newton on r(g) = F2/F0 - 3 theta (slope: the
+// variance of c^2 under W, positive) from the paper's series multiplier
+// g0 = 1/(2 theta0) - 1/(2 theta); stops when a step is below tol (1 + |g|).
+// Shell sums of c_x^4 and c_x^2 c_y^2 give <W, c_x^4> and <W, c_x^2 c_y^2> for A and B.
+template <int s>
+__host__ __device__ constexpr double shell_sum_x4() {
+  double a = 0;
+  for (int i = 0; i < kQ; ++i)
+    if (rd3q81::kDirs[i].shell == s) a += 0.0625 * rd3q81::kDirs[i].hx * rd3q81::kDirs[i].hx * rd3q81::kDirs[i].hx * rd3q81::kDirs[i].hx;
+  return a;
+}
+template <int s>
+__host__ __device__ constexpr double shell_sum_x2y2() {
+  double a = 0;
+  for (int i = 0; i < kQ; ++i)
+    if (rd3q81::kDirs[i].shell == s) a += 0.0625 * rd3q81::kDirs[i].hx * rd3q81::kDirs[i].hx * rd3q81::kDirs[i].hy * rd3q81::kDirs[i].hy;
+  return a;
+}
+
+// Per-shell factors E_s = exp(g c_s^2) / F0 (so W_s = w_s E_s), and the numerators An, Bn of
+// eq_scalars_ab for these weights.  Returns false if the iteration did not settle.
+template <class R>
+__host__ __device__ __forceinline__ bool exact_weights(R theta, const LatticeTables& tb, R* E, R& An, R& Bn) {
+  constexpr bool kDbl = sizeof(R) == sizeof(double);
+  const R tol = R(kDbl ? 1e-12 : 1e-5);
+  constexpr int kMaxIt = kDbl ? 20 : 8;
+  const R t0 = R(rd3q81::kTheta0);
+  R g = R(0.5) / t0 - R(0.5) / theta;
+  bool ok = false;
+  for (int it = 0; it < kMaxIt && !ok; ++it) {
+    R F0 = R(0), F2 = R(0), F4 = R(0);
+    static_for<kShells>([&](auto Sc) {
+      constexpr int s = decltype(Sc)::value;
+      constexpr double c2 = rd3q81::kShellC2[s];
+      constexpr double cnt = rd3q81::kShellCount[s];
+      const R ws = R(cnt) * (kDbl ? R(tb.w[s]) : R(tb.wf[s]));
+      const R v = s == 0 ? ws : ws * eexp(g * R(c2));
+      F0 += v;
+      F2 += R(c2) * v;
+      F4 += R(c2 * c2) * v;
+    });
+    const R m2 = F2 / F0;
+    const R step = (m2 - R(3) * theta) / (F4 / F0 - m2 * m2);
+    g -= step;
+    ok = fabs(step) <= tol * (R(1) + fabs(g));
+  }
+  R F0 = R(0), Mxx = R(0), Mxy = R(0);
+  static_for<kShells>([&](auto Sc) {
+    constexpr int s = decltype(Sc)::value;
+    constexpr double c2 = rd3q81::kShellC2[s];
+    E[s] = s == 0 ? R(1) : eexp(g * R(c2));
+    const R ws = kDbl ? R(tb.w[s]) : R(tb.wf[s]);
+    constexpr double sx4 = shell_sum_x4<s>(), sx2y2 = shell_sum_x2y2<s>();
+    constexpr double cnt = rd3q81::kShellCount[s];
+    F0 += R(cnt) * ws * E[s];
+    Mxx += R(sx4) * ws * E[s];
+    Mxy += R(sx2y2) * ws * E[s];
+  });
+  const R iF0 = R(1) / F0;
+#pragma unroll
+  for (int s = 0; s < kShells; ++s) E[s] *= iF0;
+  Mxx *= iF0;
+  Mxy *= iF0;
+  An = Mxx - R(3) * Mxy;
+  Bn = Mxy - theta * theta;
+  return ok && g == g;
 }
 
 // Even and odd parts (in c -> -c) of the bracket of f~eq for the +c member of pair P:
@@ -100,24 +193,34 @@ __host__ __device__ __forceinline__ void eq_pair_parts(const EqScalars<R>& e, R&
 
 // Full equilibrium of one state in arithmetic R (float or double), feq[i] in the library's
 // direction order.  With kOverW it returns feq_i / w_i instead (offset storage).
-template <class R, bool kOverW = false>
-__host__ __device__ inline void equilibrium_all(R rho, R ux, R uy, R uz, R theta, const LatticeTables& tab,
+// kExactW: the exact temperature weights W(theta) in place of the eta^4 series (returns false
+// if their 1-D iteration did not settle; always true otherwise).
+template <class R, bool kOverW = false, bool kExactW = false>
+__host__ __device__ inline bool equilibrium_all(R rho, R ux, R uy, R uz, R theta, const LatticeTables& tab,
                                                 R* feq) {
   const bool dbl = sizeof(R) == sizeof(double);
-  const R eta = theta / R(tab.theta0) - R(1);
-  R na[5], nb[5];
-  for (int k = 0; k < 5; ++k) {
-    na[k] = dbl ? R(tab.na[k]) : R(tab.naf[k]);
-    nb[k] = dbl ? R(tab.nb[k]) : R(tab.nbf[k]);
-  }
   EqScalars<R> e;
-  eq_scalars<R>(ux, uy, uz, theta, eta, na, nb, e);
   R W[kShells];
-  for (int s = 0; s < kShells; ++s) {
-    R c[5];
-    for (int k = 0; k < 5; ++k)
-      c[k] = kOverW ? (dbl ? R(tab.p[s][k]) : R(tab.pf[s][k])) : (dbl ? R(tab.wp[s][k]) : R(tab.wpf[s][k]));
-    W[s] = rho * poly4(c, eta);
+  bool ok = true;
+  if constexpr (kExactW) {
+    R An, Bn;
+    ok = exact_weights<R>(theta, tab, W, An, Bn);
+    eq_scalars_ab<R>(ux, uy, uz, theta, An, Bn, e);
+    for (int s = 0; s < kShells; ++s) W[s] *= kOverW ? rho : rho * (dbl ? R(tab.w[s]) : R(tab.wf[s]));
+  } else {
+    const R eta = theta / R(tab.theta0) - R(1);
+    R na[5], nb[5];
+    for (int k = 0; k < 5; ++k) {
+      na[k] = dbl ? R(tab.na[k]) : R(tab.naf[k]);
+      nb[k] = dbl ? R(tab.nb[k]) : R(tab.nbf[k]);
+    }
+    eq_scalars<R>(ux, uy, uz, theta, eta, na, nb, e);
+    for (int s = 0; s < kShells; ++s) {
+      R c[5];
+      for (int k = 0; k < 5; ++k)
+        c[k] = kOverW ? (dbl ? R(tab.p[s][k]) : R(tab.pf[s][k])) : (dbl ? R(tab.wp[s][k]) : R(tab.wpf[s][k]));
+      W[s] = rho * poly4(c, eta);
+    }
   }
   // rest particle: xi = psi = 0
   feq[0] = W[0] * (e.c0 + e.k0 * (R(0) - e.t3));
@@ -129,6 +232,7 @@ __host__ __device__ inline void equilibrium_all(R rho, R ux, R uy, R uz, R theta
     feq[1 + 2 * P] = W[s] * (ev + od);
     feq[2 + 2 * P] = W[s] * (ev - od);
   });
+  return ok;
 }
 
 __host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy, double uz,
@@ -151,19 +255,6 @@ __host__ __device__ inline void equilibrium_f64(double rho, double ux, double uy
 // (a BCC shell, for instance, has sum_i exp(zeta.c_i) = C_x C_y C_z), so the 15 moments cost a
 // few operations per shell; the shell factor rho w_s exp(mu + gamma c_s^2) adds one exponential
 // per shell.  The result is the same sum as the direction-by-direction one, regrouped.
-
-template <class R>
-__host__ __device__ __forceinline__ R eexp(R x) {
-  if constexpr (sizeof(R) == sizeof(double)) return exp(x); else return expf(x);
-}
-template <class R>
-__host__ __device__ __forceinline__ R elog(R x) {
-  if constexpr (sizeof(R) == sizeof(double)) return log(x); else return logf(x);
-}
-template <class R>
-__host__ __device__ __forceinline__ R esqrt(R x) {
-  if constexpr (sizeof(R) == sizeof(double)) return sqrt(x); else return sqrtf(x);
-}
 
 // Shell factor rho * ws * exp(mu + gamma c_s^2), ws = w_s (kOverW false) or 1.
 template <int s, bool kOverW, class R>

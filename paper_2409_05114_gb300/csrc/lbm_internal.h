@@ -115,12 +115,17 @@ struct Codec<__nv_bfloat16> {
 
 // Storage kinds (values match lbm_storage in include/lbm.h).
 enum StorageKind { kF64 = 0, kF32 = 1, kF16Off = 2, kBF16Off = 3 };
+// Equilibrium + collision variants of the fused kernel.
+enum Equilibrium { kEqSeries = 0, kEqEntropic = 1, kEqEntropicAlpha = 2, kEqSeriesExactW = 3 };
+RD3Q81_HD constexpr bool eq_is_series(int eq) { return eq == kEqSeries || eq == kEqSeriesExactW; }
 inline size_t storage_bytes(int s) { return s == kF64 ? 8 : s == kF32 ? 4 : 2; }
 
 // ---- launchers (each defined in the translation unit of its storage type) --------------
 // Fused pull-stream + moments + equilibrium + BGK over every interior site of both
 // sublattices.  fp64_moments selects FP64 moment sums and temperature recovery.
-// eq: 0 = series equilibrium (App. B), 1 = exact entropic equilibrium (Sec. III).
+// eq: kEqSeries (App. B equilibrium, BGK), kEqSeriesExactW (the same with the exact
+// temperature weights of Eq. (zeroveleq)), kEqEntropic (exact entropic equilibrium of Sec. III,
+// BGK) or kEqEntropicAlpha (exact entropic equilibrium, entropic alpha of Eq. (delH)).
 cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f64(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f32(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);

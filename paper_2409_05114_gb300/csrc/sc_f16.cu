@@ -1,12 +1,14 @@
 // Fused stream-collide instantiations for __half storage (one translation unit per storage
 // type so that they compile in parallel): series equilibrium with FP32 or FP64 moments, and
-// the exact entropic equilibrium.
+// the exact entropic equilibrium with BGK or entropic alpha.
 #include "stream_collide.cuh"
 
 namespace lbm {
 
 cudaError_t launch_sc_f16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s) {
   if (eq == kEqEntropic) return launch_sc<__half, false, kEqEntropic>(p, s);
+  if (eq == kEqEntropicAlpha) return launch_sc<__half, false, kEqEntropicAlpha>(p, s);
+  if (eq == kEqSeriesExactW) return launch_sc<__half, false, kEqSeriesExactW>(p, s);
   return fp64_moments ? launch_sc<__half, true>(p, s) : launch_sc<__half, false>(p, s);
 }
 

@@ -126,9 +126,136 @@ __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* 
   return Moments<M>{rho, jx, jy, jz, E};
 }
 
-// Temperature recovery, equilibrium (App. B) and BGK relaxation of one site's populations
-// f (in place), given their moments.
-enum Equilibrium { kEqSeries = 0, kEqEntropic = 1 };
+// ---- entropic alpha (Eq. (delH)) -------------------------------------------------------
+// alpha is the nontrivial root of Delta H(alpha) = H[f + alpha D] - H[f], D = feq - f, with feq
+// the exact entropic equilibrium of f's conserved moments.  Because log(feq / w) is affine in
+// (1, c, c^2) and D carries no mass, momentum or energy, <D, log(f/w)> = -<f, x log(1 + x)>
+// with x = D / f, so
+//   Delta H(alpha) = <f, (1 + alpha x) log(1 + alpha x) - alpha x> - alpha <f, x log(1 + x)>,
+// a sum of terms of order f x^2 without the cancellation between O(1) values of the plain
+// definition.  Delta H is convex in alpha, zero at 0 and negative at 1.
+// * Every |x_i| <= kX: both brackets expanded in x,
+//     Delta H(alpha) / alpha = sum_{n=2..N} (-1)^n a_n [alpha^(n-1) / (n (n-1)) - 1 / (n-1)],
+//   a_n = <f, x^n>, solved by three Newton steps from alpha = 2 (its limit as x -> 0).  The
+//   first dropped term moves the root by about 2^(N+1) x^(N-1) / (N (N+1)), which moves the
+//   update by that times beta x: below 1e-7 relative for FP32 (N = 6, |x| <= 0.05) and 1e-15
+//   for FP64 (N = 8, |x| <= 0.01).
+// * Otherwise the full expression.  alpha_max = min over x_i < 0 of -1 / x_i is where a
+//   population would reach zero; if Delta H(alpha_max) <= 0 there is no root before it and
+//   alpha = alpha_max (on coarse grids with omega near 2 this is the common case, set by a
+//   tiny outer-shell population).  Else Newton from min(2, 1 + 0.9 (alpha_max - 1)),
+//   safeguarded by bisection on [1, alpha_max]; it stops once a Newton step or the bracket is
+//   below the tolerance (near equilibrium the rounding of Delta H decides which comes first).
+// * A population <= 0 (H undefined) or D = 0: alpha = 2.
+
+template <class R>
+__device__ __forceinline__ R elog1p(R x) {
+  if constexpr (std::is_same_v<R, double>) return log1p(x); else return log1pf(x);
+}
+template <class R>
+__device__ __forceinline__ R ratio(R a, R b) {
+  if constexpr (std::is_same_v<R, double>) return a / b; else return __fdividef(a, b);
+}
+
+// Calls fn(F, E, wgt) for every direction: F = f_i and E = feq_i (plain storage), or
+// F = f_i / w_i and E = feq_i / w_i with wgt = w_i (offset storage; wgt = 1 otherwise), feq the
+// exact entropic equilibrium with multipliers lam.
+template <class Store, class R, class Fn>
+__device__ __forceinline__ void visit_populations(const R* f, const R* lam, R rho, const LatticeTables& tb, Fn&& fn) {
+  constexpr bool kOff = Codec<Store>::kOffset;
+  fn(kOff ? R(1) + f[0] : f[0], entropic_shell_factor<0, kOff>(lam, rho, tb), kOff ? tab_w<R>(tb, 0) : R(1));
+  entropic_pair_values<R, kOff>(lam, rho, tb, [&](auto Pc, R vp, R vm) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr int s = rd3q81::kDirs[1 + 2 * P].shell;
+    const R wg = kOff ? tab_w<R>(tb, s) : R(1);
+    fn(kOff ? R(1) + f[1 + 2 * P] : f[1 + 2 * P], vp, wg);
+    fn(kOff ? R(1) + f[2 + 2 * P] : f[2 + 2 * P], vm, wg);
+  });
+}
+
+template <class Store, class R>
+__device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho, const LatticeTables& tb, R amax) {
+  constexpr bool kDbl = std::is_same_v<R, double>;
+  constexpr int kMaxIt = kDbl ? 60 : 30;
+  const R tol = R(kDbl ? 1e-14 : 1e-6);
+  // b = <f, x log(1 + x)>; Delta H(alpha_max) (the limiting population's term is 1 there)
+  R b = R(0), Sm = R(0);
+  visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
+    const R x = ratio(E - F, F);
+    const R y = amax * x;
+    b += wg * F * x * elog1p(x);
+    Sm += wg * F * (y > R(-1) ? (R(1) + y) * elog1p(y) - y : R(1));
+  });
+  if (amax < R(1e30) && Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
+  R lo = R(1), hi = amax;
+  R al = fmin(R(2), R(1) + R(0.9) * (amax - R(1)));
+  for (int it = 0; it < kMaxIt; ++it) {
+    R S = R(0), dS = R(0);
+    visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
+      const R x = ratio(E - F, F);
+      const R y = al * x;
+      const R l = elog1p(y);
+      S += wg * F * ((R(1) + y) * l - y);
+      dS += wg * F * x * l;
+    });
+    const R Fv = S - al * b, dF = dS - b;
+    if (Fv < R(0)) lo = al; else hi = al;
+    const R step = Fv / dF;
+    if (fabs(step) <= tol * al) return al - step;  // converged (also when Fv == 0)
+    R nx = al - step;
+    if (!(nx > lo && nx < hi)) nx = R(0.5) * (lo + hi);
+    al = nx;
+    if (hi - lo <= tol * al) break;                 // bracket at the rounding of Delta H
+  }
+  return al;
+}
+
+template <class Store, class R>
+__device__ __forceinline__ R entropic_alpha(const R* f, const R* lam, R rho, const LatticeTables& tb) {
+  constexpr bool kDbl = std::is_same_v<R, double>;
+  constexpr int N = kDbl ? 8 : 6;
+  const R kX = R(kDbl ? 0.01 : 0.05);
+  R an[N - 1];  // a_2 .. a_N
+#pragma unroll
+  for (int k = 0; k < N - 1; ++k) an[k] = R(0);
+  R xmin = R(0), xabs = R(0), Fmin = R(1);
+  visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
+    const R x = ratio(E - F, F);
+    Fmin = fmin(Fmin, F);
+    xmin = fmin(xmin, x);
+    xabs = fmax(xabs, fabs(x));
+    R pw = wg * F * x;
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) {
+      pw *= x;
+      an[k] += pw;
+    }
+  });
+  if (!(Fmin > R(0)) || !(an[0] > R(0))) return R(2);
+  R al = R(2);
+  if (xabs <= kX) {
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      R G = R(0), dG = R(0), pw = R(1);  // pw = al^(n-2)
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        const int n = k + 2;
+        const R sa = (n % 2 == 0) ? an[k] : -an[k];
+        G += sa * (pw * al * R(1.0 / (n * (n - 1))) - R(1.0 / (n - 1)));
+        dG += sa * pw * R(1.0 / n);
+        pw *= al;
+      }
+      al -= G / dG;
+    }
+  } else {
+    al = entropic_alpha_full<Store>(f, lam, rho, tb, xmin < R(0) ? R(-1) / xmin : R(1e30));
+  }
+  return (al > R(0) && al < R(1e30)) ? al : R(2);
+}
+
+// Temperature recovery, equilibrium (App. B series, or the exact one of Sec. III) and the
+// collision (alpha = 2, or the entropic alpha) of one site's populations f (in place), given
+// their moments.
 
 template <class Store, class M, int kEq = kEqSeries>
 __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const Moments<M>& mo, double omega,
@@ -152,12 +279,22 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
 #pragma unroll
     for (int s = 0; s < kShells; ++s)
       W[s] = rh * poly4(C::kOffset ? tab_p<R>(tb, s) : tab_wp<R>(tb, s), eta);
+  } else if constexpr (kEq == kEqSeriesExactW) {
+    R An, Bn;
+    if (!exact_weights<R>(theta, tb, W, An, Bn)) atomicOr(flag, 1u);
+    eq_scalars_ab<R>(R(mux), R(muy), R(muz), theta, An, Bn, e);
+#pragma unroll
+    for (int s = 0; s < kShells; ++s) W[s] *= C::kOffset ? rh : rh * tab_w<R>(tb, s);
   } else {
     constexpr bool kDbl = std::is_same_v<R, double>;
     const R T[5] = {rh, R(mo.jx), R(mo.jy), R(mo.jz), R(mo.E)};
     if (!entropic_multipliers<R>(T, R(mux), R(muy), R(muz), theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam))
       atomicOr(flag, 1u);
   }
+
+  // ---- entropic alpha (Eq. (delH)) or alpha = 2 --------------------------------------------
+  [[maybe_unused]] R alpha = R(2);
+  if constexpr (kEq == kEqEntropicAlpha) alpha = entropic_alpha<Store>(f, lam, rh, tb);
 
   // ---- BGK collision, Eq. (discretelbm) -------------------------------------------------
   // f_i <- f_i + omega D_i with D_i = f~eq_i - f_i.  In exact arithmetic D has zero mass,
@@ -170,7 +307,8 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   // part (with omega near 2 such a part would hardly decay).  The result equals the plain
   // update in exact arithmetic; in FP32 it conserves to the rounding of the defect sums.
   constexpr bool kProject = std::is_same_v<Store, float>;
-  const R om = R(omega);
+  R om = R(omega);                   // alpha beta with alpha = 2
+  if constexpr (kEq == kEqEntropicAlpha) om = R(0.5) * om * alpha;
   R d1 = R(0), dE = R(0), dx = R(0), dy = R(0), dz = R(0);
   auto relax_rest = [&](R feq0) {
     if constexpr (C::kOffset) feq0 -= R(1);
@@ -199,7 +337,7 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     f[1 + 2 * P] += om * Dp;
     f[2 + 2 * P] += om * Dm;
   };
-  if constexpr (kEq == kEqSeries) {
+  if constexpr (eq_is_series(kEq)) {
     relax_rest(W[0] * (e.c0 + e.k0 * (R(0) - e.t3)));
     static_for<kPairs>([&](auto Pc) {
       constexpr int P = decltype(Pc)::value;
@@ -215,7 +353,30 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     relax_rest(entropic_shell_factor<0, C::kOffset>(lam, rh, tb));
     entropic_pair_values<R, C::kOffset>(lam, rh, tb, relax_pair);
   }
-  if constexpr (kProject) {
+  if constexpr (kProject && kEq == kEqEntropicAlpha) {
+    // With the entropic alpha the update of the smallest populations decides alpha, so their
+    // correction must be small relative to them: the defects are removed by subtracting
+    // omega feq_i (k . phi_i), k from <feq, phi phi^T> k = defects (the Newton's 5x5 matrix at
+    // the final multipliers).  In exact arithmetic the defects and k are zero.
+    R J[15];
+    entropic_moment_matrix<R>(lam, rh, tb, J);
+    R k[5] = {d1, dx, dy, dz, dE};
+    if (solve_spd5<R>(J, k)) {
+      f[0] -= om * entropic_shell_factor<0, false>(lam, rh, tb) * k[0];
+      entropic_pair_values<R, false>(lam, rh, tb, [&](auto Pc, R vp, R vm) {
+        constexpr int P = decltype(Pc)::value;
+        constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+        constexpr double c2 = rd3q81::kShellC2[d.shell];
+        const R ev = k[0] + R(c2) * k[4];
+        R od = R(0);
+        if constexpr (d.hx != 0) od += R(0.5 * d.hx) * k[1];
+        if constexpr (d.hy != 0) od += R(0.5 * d.hy) * k[2];
+        if constexpr (d.hz != 0) od += R(0.5 * d.hz) * k[3];
+        f[1 + 2 * P] -= om * vp * (ev + od);
+        f[2 + 2 * P] -= om * vm * (ev - od);
+      });
+    }
+  } else if constexpr (kProject) {
     constexpr double t0 = rd3q81::kTheta0;
     const R g = (dE - R(3.0 * t0) * d1) * R(1.0 / (6.0 * t0 * t0));
     const R a = d1 - R(3.0 * t0) * g;
@@ -300,7 +461,7 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 template <class Store, bool kF64Mom, int kEq>
 constexpr int sc_min_blocks() {
   if constexpr (std::is_same_v<Store, double>) return 1;
-  else if constexpr (kF64Mom) return 3;
+  else if constexpr (kF64Mom || kEq == kEqEntropicAlpha) return 3;
   else return 4;
 }
 

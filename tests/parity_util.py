@@ -31,17 +31,18 @@ def lib_perm():
     return np.array([idx[tuple(int(x) for x in v)] for v in h])
 
 
-def oracle_run(wl, steps: int, tau: float, eq: str = "series"):
+def oracle_run(wl, steps: int, tau: float, eq: str = "series", collision: str = "bgk"):
     f = O.init(wl.rho, wl.u, wl.theta, eq=eq)
-    f = O.run(f, tau, steps, wl.oracle_bc_x(), eq=eq)
+    f = O.run(f, tau, steps, wl.oracle_bc_x(), eq=eq, collision=collision)
     return f
 
 
 def gpu_run(wl, steps: int, tau: float, storage: str, fp64_moments=False, populations=None, eq="series",
-            check_stable=False):
+            check_stable=False, collision="bgk"):
     """Returns (f_lib[2, 81, z, y, x] in library order, rho, u, theta) after `steps`."""
     from paper_2409_05114_gb300 import binding as B
-    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, fp64_moments, equilibrium=eq)
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, fp64_moments, equilibrium=eq,
+                        collision=collision)
     ctx = B.lbm_create(cfg)
     try:
         if populations is None:

@@ -91,6 +91,21 @@ def test_bad_face_kind_rejected(B):
         B.lbm_footprint(cfg)
 
 
+def test_equilibrium_and_collision_validation(B):
+    for kw in (dict(equilibrium="entropic", collision="entropic"), dict(equilibrium="series_exact_w"),
+               dict(equilibrium="series", fp64_moments=True)):
+        assert B.lbm_footprint(B.make_config(16, 8, 4, 0.1, "f32", **kw)) > 0
+    for kw in (dict(equilibrium="series", collision="entropic"),            # alpha needs the exact equilibrium
+               dict(equilibrium="series_exact_w", collision="entropic"),
+               dict(equilibrium="entropic", collision=5),
+               dict(equilibrium=3),
+               dict(equilibrium="entropic", fp64_moments=True),
+               dict(equilibrium="series_exact_w", fp64_moments=True)):
+        with pytest.raises(B.LbmError) as ei:
+            B.lbm_footprint(B.make_config(16, 8, 4, 0.1, "f32", **kw))
+        assert ei.value.status == B.LBM_EINVAL
+
+
 def test_null_context_calls_are_einval(B):
     import ctypes
     lib = B._lib

@@ -1,0 +1,124 @@
+"""GPU parity of the entropic alpha (Eq. (delH); config collision = LBM_COLLISION_ENTROPIC with
+the exact entropic equilibrium) against the oracle's root of Delta H, and the discrete H
+theorem it exists for.
+
+Tolerances: FP64 -- both sides solve for alpha to round-off (the kernel's series branch
+truncates below 1e-15 relative), so populations within 1e-10 of the weights; FP32/FP16 as
+for the entropic equilibrium with BGK (fields within 1e-5 / 2e-3 after 20 steps)."""
+
+import numpy as np
+import pytest
+
+from parity_util import ensure_built, field_errors, gpu_run, lib_perm, oracle_run, population_error
+from oracle import rd3q81 as O
+from paper_2409_05114_gb300 import workloads as W
+from riemann_exact import sample
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    ensure_built()
+    from paper_2409_05114_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def perm(B):
+    return lib_perm()
+
+
+@pytest.fixture(scope="module")
+def wlib(B):
+    return B.lbm_velocities()[1]
+
+
+@pytest.mark.parametrize("dims,steps,mach,tau", [((10, 8, 6), 4, 0.5, 0.1), ((13, 3, 2), 3, 1.5, 0.1),
+                                                  ((8, 6, 4), 5, 0.5, 0.01)])
+def test_fp64_alpha_parity(B, perm, wlib, dims, steps, mach, tau):
+    wl = W.smooth_random(*dims, seed=23, mach=mach, eta=0.15)
+    f_or = oracle_run(wl, steps, tau, eq="entropic", collision="entropic")
+    f, r, u, t = gpu_run(wl, steps, tau, "f64", eq="entropic", collision="entropic", check_stable=True)
+    err = population_error(f_or[:, perm], f, wlib)
+    print("alpha f64 %s %d steps tau %g: population error %.3g" % (dims, steps, tau, err))
+    assert err <= 1e-10
+    er = field_errors(O.fields(f_or), (r, u, t))
+    assert max(er) <= 1e-10, er
+
+
+def test_alpha_differs_from_bgk(B):
+    """On a coarse TGV with omega near 2 the root is far from 2 at most sites (a tiny
+    outer-shell population limits it), so the two collisions give different fields."""
+    wl = W.taylor_green(12, mach=0.5)
+    tau = wl.paper_tau("lb")
+    _, r1, u1, t1 = gpu_run(wl, 5, tau, "f64", eq="entropic", collision="entropic")
+    _, r2, u2, t2 = gpu_run(wl, 5, tau, "f64", eq="entropic", collision="bgk")
+    assert np.max(np.abs(t1 - t2) / t2) > 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 2e-3)])
+def test_alpha_storage_parity_tgv(B, storage, tol):
+    wl = W.taylor_green(16, mach=0.5)
+    tau = wl.paper_tau("lb")
+    ref = O.fields(oracle_run(wl, 20, tau, eq="entropic", collision="entropic"))
+    _, r, u, t = gpu_run(wl, 20, tau, storage, eq="entropic", collision="entropic", check_stable=True)
+    er = field_errors(ref, (r, u, t))
+    print("alpha %s TGV16 20 steps: rel err rho %.3g u %.3g theta %.3g" % (storage, *er))
+    assert max(er) <= tol, er
+
+
+def test_h_theorem_on_gpu(B, perm):
+    """Periodic grid, FP64, off-equilibrium start: the total H of the populations the library
+    holds never grows from step to step (streaming permutes, the entropic collision with
+    beta <= 1 cannot raise a site's H)."""
+    wl = W.smooth_random(8, 6, 5, seed=5, mach=0.5, eta=0.1)
+    rng = np.random.default_rng(9)
+    f0 = O.init(wl.rho, wl.u, wl.theta, eq="entropic")
+    f0 = f0 * np.exp(0.05 * rng.uniform(-1, 1, f0.shape))
+    lib = np.ascontiguousarray(f0[:, perm])
+    w = O.velocity_set().w[perm].reshape(1, 81, 1, 1, 1)
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, 0.02, "f64", wl.faces, equilibrium="entropic", collision="entropic")
+    ctx = B.lbm_create(cfg)
+    try:
+        B.lbm_set_populations(ctx, lib.reshape(-1))
+        hs = []
+        for _ in range(8):
+            f = np.zeros(lib.size)
+            B.lbm_get_populations(ctx, f)
+            f = f.reshape(lib.shape)
+            hs.append(float((f * (np.log(f / w) - 1)).sum()))
+            B.lbm_step(ctx, 1)
+        B.lbm_sync(ctx)
+    finally:
+        B.lbm_destroy(ctx)
+    d = np.diff(hs)
+    assert np.all(d <= 1e-12 * abs(hs[0])), d
+
+
+def test_mach2_blob_with_alpha(B):
+    wl = W.mach2_blob(64, 16, 4)
+    tau = wl.paper_tau("literal")
+    ref = O.fields(oracle_run(wl, 10, tau, eq="entropic", collision="entropic"))
+    _, r, u, t = gpu_run(wl, 10, tau, "f32", eq="entropic", collision="entropic", check_stable=True)
+    er = field_errors(ref, (r, u, t))
+    print("alpha f32 Mach-2 blob 10 steps: rel err rho %.3g u %.3g theta %.3g" % er)
+    assert max(er) <= 1e-4, er
+    _, r, u, t = gpu_run(wl, 300, tau, "f32", eq="entropic", collision="entropic", check_stable=True)
+    assert np.all(np.isfinite(r)) and np.all(t > 0)
+
+
+def test_strong_sod_with_alpha_matches_riemann(B):
+    nx, steps = 512, 100
+    wl = W.sod(nx=nx, ny=1, nz=1)
+    _, r, u, t = gpu_run(wl, steps, wl.paper_tau("lb"), "f32", eq="entropic", collision="entropic",
+                         check_stable=True)
+    x = np.concatenate([np.arange(nx) + 0.0, np.arange(nx) + 0.5])
+    o = np.argsort(x)
+    x, R, U, P = x[o], r.reshape(-1)[o], u[0].reshape(-1)[o], (r * t).reshape(-1)[o]
+    re, ue, pe, info = sample((1.0, 0.0, W.THETA0), (0.125, 0.0, 0.1 * W.THETA0), 5.0 / 3.0, (x - nx / 2) / steps)
+    x_shock = x[np.where(R > 0.5 * (info["rho_star_right"] + 0.125))[0].max()]
+    assert abs(x_shock - (nx / 2 + info["s_shock"] * steps)) < 3.0
+    plateau = (x > nx / 2 + info["s_tail"] * steps + 8) & (x < nx / 2 + info["s_shock"] * steps - 8)
+    assert abs(U[plateau].mean() / info["u_star"] - 1) < 0.02
+    assert abs(P[plateau].mean() / info["p_star"] - 1) < 0.02
