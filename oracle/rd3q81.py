@@ -31,6 +31,8 @@ read against the paper line by line:
                           entropic alpha, beta = dt / (2 tau + dt) with dt = 1.
 * ``entropic_alpha``      Sec. II, Eq. (delH): the nontrivial root of
                           H[f + alpha (feq - f)] - H[f] = 0 (``entropic_delta_h``).
+* ``diagnostics``         Sec. IV C: mean kinetic energy and mean enstrophy (curl by central
+                          differences on each sublattice).
 * ``fill_ghosts_x``       Boundary layers in x.  The paper names its own boundary
                           conditions without formulas; this oracle implements the three the
                           library offers (periodic, zero-gradient outflow, equilibrium
@@ -664,6 +666,40 @@ def fields(f: np.ndarray, lat: Lattice | None = None):
     """(rho[2,z,y,x], u[3,2,z,y,x], theta[2,z,y,x]) of stored populations f[s, i, z, y, x]."""
     lat = lat or velocity_set()
     return moments(np.moveaxis(f, 1, 0), lat)
+
+
+def _central_diff(a: np.ndarray, axis: int, periodic: bool) -> np.ndarray:
+    """d a / d(index) along ``axis`` by second-order central differences (unit spacing);
+    on a non-periodic axis the two end planes take second-order one-sided differences."""
+    if periodic:
+        return 0.5 * (np.roll(a, -1, axis=axis) - np.roll(a, 1, axis=axis))
+    a = np.moveaxis(a, axis, 0)
+    d = np.empty_like(a)
+    d[1:-1] = 0.5 * (a[2:] - a[:-2])
+    d[0] = -1.5 * a[0] + 2.0 * a[1] - 0.5 * a[2]
+    d[-1] = 1.5 * a[-1] - 2.0 * a[-2] + 0.5 * a[-3]
+    return np.moveaxis(d, 0, axis)
+
+
+def diagnostics(f: np.ndarray, lat: Lattice | None = None, x_periodic: bool = True):
+    """Mean kinetic energy and mean enstrophy of Sec. IV C (compressible Taylor-Green vortex):
+
+        KE = (1/|Omega|) int rho u.u / 2 dOmega,   eps = (1/|Omega|) int rho w.w / 2 dOmega,
+        w = curl u,
+
+    as averages over all sites of both sublattices.  The paper gives no discretisation of the
+    curl; here each sublattice is differentiated on its own grid (unit spacing, second-order
+    central differences; y and z periodic, x periodic or with one-sided second-order end
+    differences).  f[s, i, z, y, x]; returns (KE, eps)."""
+    rho, u, _ = fields(f, lat)                          # rho[s,z,y,x], u[a,s,z,y,x]
+    ke = (0.5 * rho * (u ** 2).sum(axis=0)).mean()
+    # axis of u[a] arrays: s=0, z=1, y=2, x=3
+    d = lambda comp, ax: _central_diff(u[comp], {"x": 3, "y": 2, "z": 1}[ax], x_periodic or ax != "x")
+    wx = d(2, "y") - d(1, "z")
+    wy = d(0, "z") - d(2, "x")
+    wz = d(1, "x") - d(0, "y")
+    ens = (0.5 * rho * (wx ** 2 + wy ** 2 + wz ** 2)).mean()
+    return float(ke), float(ens)
 
 
 def totals(f: np.ndarray, lat: Lattice | None = None):
