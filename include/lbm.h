@@ -141,6 +141,23 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n);
  * the fields) if any step so far was flagged. */
 lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int on_device);
 
+/* Mean kinetic energy and mean enstrophy of the stored state (Sec. IV C, compressible
+ * Taylor-Green vortex): out2[0] = KE = <rho u.u / 2>, out2[1] = eps = <rho w.w / 2>, w = curl u,
+ * averages over all 2 nx ny nz sites (host memory, 2 doubles).  The paper gives no
+ * discretisation of the curl: it is taken on each sublattice's own grid (unit spacing) by
+ * second-order central differences; y and z wrap, x wraps when the x faces are periodic and
+ * otherwise uses second-order one-sided differences at the end planes.  FP64 fields and
+ * deterministic sums.  Allocates 40 bytes per site of device memory for the call (stream-
+ * ordered, freed before it returns); synchronises.  LBM_EINVAL: NULL out2, context not
+ * initialised, or non-periodic x with nx < 3; LBM_ENOMEM: no room for the fields. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, double* out2);
+
+/* Self-check, no counterpart in the paper: the largest relative difference between the FP32
+ * log(1 + y) that the entropic-alpha solve uses and CUDA's log1pf over n points of a fixed sweep
+ * of y in (-0.999, 100), written to *max_rel_err (host).  Runs on the current device and
+ * synchronises.  LBM_EINVAL: n < 1 or NULL output; LBM_ENOMEM / LBM_ECUDA on device errors. */
+lbm_status lbm_selftest_log1p(long long n, double* max_rel_err);
+
 /* Global sums over all sites of rho, rho u_x, rho u_y, rho u_z and <f, c^2>, FP64,
  * bitwise reproducible for a given state (fixed reduction order).  out5: host double[5].
  * Synchronises. */

@@ -74,6 +74,8 @@ def _load():
         "lbm_step": ([P, LL], I),
         "lbm_moments": ([P, P, P, P, I], I),
         "lbm_totals": ([P, P], I),
+        "lbm_diagnostics": ([P, P], I),
+        "lbm_selftest_log1p": ([LL, ctypes.POINTER(D)], I),
         "lbm_get_populations": ([P, P, I], I),
         "lbm_set_populations": ([P, P, I], I),
         "lbm_probe": ([P, P, LL, P], I),
@@ -195,6 +197,20 @@ def lbm_totals(ctx) -> np.ndarray:
     out = np.zeros(5)
     _check(_lib.lbm_totals(ctx, ctypes.c_void_p(out.ctypes.data)), ctx)
     return out
+
+
+def lbm_diagnostics(ctx):
+    """(KE, enstrophy): mean rho u.u/2 and mean rho |curl u|^2/2 of the stored state (Sec. IV C)."""
+    out = np.zeros(2)
+    _check(_lib.lbm_diagnostics(ctx, ctypes.c_void_p(out.ctypes.data)), ctx)
+    return float(out[0]), float(out[1])
+
+
+def lbm_selftest_log1p(n: int = 1 << 24) -> float:
+    """Largest relative difference of the entropic-alpha FP32 log(1 + y) from CUDA's log1pf."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.lbm_selftest_log1p(n, ctypes.byref(out)), None)
+    return out.value
 
 
 def lbm_get_populations(ctx, f):

@@ -416,6 +416,37 @@ lbm_status lbm_totals(lbm_ctx* ctx, double* out5) {
   return LBM_OK;
 }
 
+lbm_status lbm_diagnostics(lbm_ctx* ctx, double* out2) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!out2) return fail(ctx, LBM_EINVAL, "out2 is NULL");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  if (!ctx->g.x_periodic && ctx->cfg.nx < 3)
+    return fail(ctx, LBM_EINVAL, "the one-sided x differences of a non-periodic grid need nx >= 3");
+  DeviceGuard dg(ctx->device);
+  const long long S = ctx->sites;
+  const long long nb = lbm::diagnostics_blocks(S);
+  const size_t bytes = static_cast<size_t>(5 * S + 2 * nb + 2) * sizeof(double);
+  void* scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, LBM_ENOMEM, "no device memory for the diagnostics fields (40 bytes per site)");
+  }
+  double* rho = static_cast<double*>(scratch);
+  double* u = rho + S;
+  double* theta = u + 3 * S;
+  double* partials = theta + S;
+  double* dout = partials + 2 * nb;
+  cudaError_t e = lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], rho, u, theta, 0, S, S,
+                                      ctx->stream);
+  if (e == cudaSuccess) e = lbm::launch_diagnostics(ctx->g, rho, u, S, partials, dout, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out2, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  ctx->launches += 3;
+  cudaFreeAsync(scratch, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, std::string("lbm_diagnostics: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, int on_device) {
   if (!valid(ctx)) return LBM_EINVAL;
   if (!f) return fail(ctx, LBM_EINVAL, "f is NULL");

@@ -153,6 +153,13 @@ cudaError_t launch_set_populations(int storage, const Geometry& g, const Lattice
                                    const double* f, long long first, long long count, cudaStream_t s);
 cudaError_t launch_totals(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
                           double* partials, int nblocks, double* out5, cudaStream_t s);
+
+// Mean kinetic energy and enstrophy (Sec. IV C) from FP64 fields rho[sites], u[3][sites] (sites
+// ordered sub, z, y, x); partials holds 2 * diagnostics_blocks(sites) doubles; out2 (device) gets
+// {KE, eps}.  Two launches (diagnostics.cu).
+long long diagnostics_blocks(long long sites);
+cudaError_t launch_diagnostics(const Geometry& g, const double* rho, const double* u, long long sites,
+                               double* partials, double* out2, cudaStream_t s);
 int totals_blocks(const Geometry& g);
 cudaError_t launch_probe(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
                          const long long* sites, long long count, double* f, cudaStream_t s);

@@ -149,10 +149,6 @@ __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* 
 // * A population <= 0 (H undefined) or D = 0: alpha = 2.
 
 template <class R>
-__device__ __forceinline__ R elog1p(R x) {
-  if constexpr (std::is_same_v<R, double>) return log1p(x); else return log1pf(x);
-}
-template <class R>
 __device__ __forceinline__ R ratio(R a, R b) {
   if constexpr (std::is_same_v<R, double>) return a / b; else return __fdividef(a, b);
 }
@@ -173,41 +169,110 @@ __device__ __forceinline__ void visit_populations(const R* f, const R* lam, R rh
   });
 }
 
+// log(1 + y) for y > -1, FP32: for |y| < 1/4 from log(1 + y) = 2 atanh(s), s = y / (2 + y)
+// (|s| <= 1/7; the odd series to s^9 leaves below 1e-9 relative); otherwise the hardware
+// logarithm of u = 1 + y, corrected for the rounding of u by (y - (u - 1)) / u.  Relative error
+// below 2e-6 everywhere (the hardware log2 is good to 2^-21 absolute on [1/2, 2]).
+__device__ __forceinline__ float log1p_alpha(float y) {
+  const float u = 1.0f + y;
+  if (fabsf(y) < 0.25f) {
+    const float s = __fdividef(y, 2.0f + y), s2 = s * s;
+    return 2.0f * s * (1.0f + s2 * (1.0f / 3.0f + s2 * (0.2f + s2 * (1.0f / 7.0f + s2 * (1.0f / 9.0f)))));
+  }
+  return __logf(u) + __fdividef(y - (u - 1.0f), u);
+}
+__device__ __forceinline__ double log1p_alpha(double y) { return log1p(y); }
+
+// The full-expression solve.  The walk runs once, to collect x_i and w_i F_i in a per-thread
+// (local-memory) array; the sums over directions are then short runtime loops (an unrolled
+// evaluation per iterate would not fit the instruction cache).
+// Each pass expands Delta H about a centre a0 exactly in delta = alpha - a0: with u_i = 1 + a0 x_i,
+// L_i = log u_i and z_i = x_i / u_i,
+//   Delta H(a0 + delta) = F0 + F1 delta + sum_{n>=2} (-1)^n M_n delta^n / (n (n-1)),
+//   F0 = <f, u L - a0 x> - a0 b,  F1 = <f, x L> - b,  M_n = <f, u z^n>,
+// which converges for q = |delta| max|z| < 1, the terms beyond n = N summing to at most
+// |delta|^(N+1) <f, u |z|^(N+1)> / (N (N+1) (1 - q)).  The root of the series truncated at N
+// (Newton from 0) is accepted when that bound moves alpha by less than the tolerance (divided
+// by the slope F1), or when delta itself is below it; otherwise the root becomes the next centre,
+// kept inside the bracket [lo, hi] that the signs of F0 maintain (bisection when it would leave
+// it).  One pass usually suffices: populations with large |z| weigh little in the bound.
 template <class Store, class R>
 __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho, const LatticeTables& tb, R amax) {
   constexpr bool kDbl = std::is_same_v<R, double>;
-  constexpr int kMaxIt = kDbl ? 60 : 30;
+  constexpr int N = kDbl ? 10 : 6;
+  constexpr int kMaxPass = kDbl ? 40 : 20;
   const R tol = R(kDbl ? 1e-14 : 1e-6);
+  R xs[kQ], wf[kQ];
+  int n = 0;
+  visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
+    xs[n] = ratio(E - F, F);
+    wf[n] = wg * F;
+    ++n;
+  });
   // b = <f, x log(1 + x)>; Delta H(alpha_max) (the limiting population's term is 1 there)
   R b = R(0), Sm = R(0);
-  visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
-    const R x = ratio(E - F, F);
-    const R y = amax * x;
-    b += wg * F * x * elog1p(x);
-    Sm += wg * F * (y > R(-1) ? (R(1) + y) * elog1p(y) - y : R(1));
-  });
+#pragma unroll 1
+  for (int i = 0; i < kQ; ++i) {
+    const R x = xs[i], y = amax * x;
+    b += wf[i] * x * log1p_alpha(x);
+    Sm += wf[i] * (y > R(-1) ? (R(1) + y) * log1p_alpha(y) - y : R(1));
+  }
   if (amax < R(1e30) && Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
   R lo = R(1), hi = amax;
-  R al = fmin(R(2), R(1) + R(0.9) * (amax - R(1)));
-  for (int it = 0; it < kMaxIt; ++it) {
-    R S = R(0), dS = R(0);
-    visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
-      const R x = ratio(E - F, F);
-      const R y = al * x;
-      const R l = elog1p(y);
-      S += wg * F * ((R(1) + y) * l - y);
-      dS += wg * F * x * l;
-    });
-    const R Fv = S - al * b, dF = dS - b;
-    if (Fv < R(0)) lo = al; else hi = al;
-    const R step = Fv / dF;
-    if (fabs(step) <= tol * al) return al - step;  // converged (also when Fv == 0)
-    R nx = al - step;
-    if (!(nx > lo && nx < hi)) nx = R(0.5) * (lo + hi);
-    al = nx;
-    if (hi - lo <= tol * al) break;                 // bracket at the rounding of Delta H
+  R a0 = fmin(R(2), R(1) + R(0.9) * (amax - R(1)));
+  for (int pass = 0; pass < kMaxPass; ++pass) {
+    R F0 = R(0), F1 = R(0), zmax = R(0), Mabs = R(0), M[N - 1];  // M[k] = M_{k+2}
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) M[k] = R(0);
+#pragma unroll 1
+    for (int i = 0; i < kQ; ++i) {
+      const R x = xs[i], y = a0 * x, u = R(1) + y;
+      const R L = log1p_alpha(y);
+      const R z = ratio(x, u);
+      F0 += wf[i] * (u * L - y);
+      F1 += wf[i] * x * L;
+      zmax = fmax(zmax, fabs(z));
+      R t = wf[i] * u * z;
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        t *= z;
+        M[k] += t;
+      }
+      Mabs += fabs(t * z);
+    }
+    F0 -= a0 * b;
+    F1 -= b;
+    if (F0 < R(0)) lo = a0; else hi = a0;
+    // root of the truncated series: Newton in delta from 0
+    R d = R(0);
+    for (int it = 0; it < 8; ++it) {
+      R G = F0 + F1 * d, dG = F1, p = d;             // p = d^(n-1)
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        const int nn = k + 2;
+        const R c = ((nn % 2 == 0) ? R(1) : R(-1)) * M[k];
+        dG += c * p * R(1.0 / (nn - 1));
+        p *= d;
+        G += c * p * R(1.0 / (nn * (nn - 1)));
+      }
+      const R step = G / dG;
+      d -= step;
+      if (!(fabs(step) > tol * a0)) break;
+    }
+    const R na = a0 + d;
+    const R q = fabs(d) * zmax;
+    R bound = R(1e30);
+    if (q < R(1)) {
+      bound = Mabs / (R(N * (N + 1)) * (R(1) - q));
+#pragma unroll
+      for (int k = 0; k <= N; ++k) bound *= fabs(d);
+    }
+    const bool inside = na > lo && na < hi;
+    if (inside && (bound <= tol * fabs(F1) * a0 || fabs(d) <= tol * a0)) return na;
+    a0 = inside ? na : R(0.5) * (lo + hi);
+    if (hi - lo <= tol * a0) break;
   }
-  return al;
+  return a0;
 }
 
 template <class Store, class R>

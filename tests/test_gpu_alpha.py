@@ -122,3 +122,11 @@ def test_strong_sod_with_alpha_matches_riemann(B):
     plateau = (x > nx / 2 + info["s_tail"] * steps + 8) & (x < nx / 2 + info["s_shock"] * steps - 8)
     assert abs(U[plateau].mean() / info["u_star"] - 1) < 0.02
     assert abs(P[plateau].mean() / info["p_star"] - 1) < 0.02
+
+
+def test_alpha_log1p_against_cuda(B):
+    """The FP32 log(1 + y) of the entropic-alpha solve (2 atanh(y/(2+y)) series below |y| = 1/4,
+    the hardware log with a rounding correction above) stays within 2e-6 of CUDA's log1pf."""
+    err = B.lbm_selftest_log1p(1 << 22)
+    print("log1p_alpha max relative difference from log1pf: %.3g" % err)
+    assert err <= 2e-6
