@@ -209,30 +209,31 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
     wf[n] = wg * F;
     ++n;
   });
-  // b = <f, x log(1 + x)>; Delta H(alpha_max) (the limiting population's term is 1 there)
-  R b = R(0), Sm = R(0);
-#pragma unroll 1
-  for (int i = 0; i < kQ; ++i) {
-    const R x = xs[i], y = amax * x;
-    b += wf[i] * x * log1p_alpha(x);
-    Sm += wf[i] * (y > R(-1) ? (R(1) + y) * log1p_alpha(y) - y : R(1));
-  }
-  if (amax < R(1e30) && Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
   R lo = R(1), hi = amax;
   R a0 = fmin(R(2), R(1) + R(0.9) * (amax - R(1)));
+  R b = R(0);
   for (int pass = 0; pass < kMaxPass; ++pass) {
+    // the first pass also sums b = <f, x log(1 + x)> and Delta H(alpha_max) (the limiting
+    // population's term is 1 there)
+    R Sm = R(0);
     R F0 = R(0), F1 = R(0), zmax = R(0), Mabs = R(0), M[N - 1];  // M[k] = M_{k+2}
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) M[k] = R(0);
 #pragma unroll 1
     for (int i = 0; i < kQ; ++i) {
-      const R x = xs[i], y = a0 * x, u = R(1) + y;
+      const R x = xs[i], w = wf[i];
+      if (pass == 0) {
+        const R ym = amax * x;
+        b += w * x * log1p_alpha(x);
+        Sm += w * (ym > R(-1) ? (R(1) + ym) * log1p_alpha(ym) - ym : R(1));
+      }
+      const R y = a0 * x, u = R(1) + y;
       const R L = log1p_alpha(y);
       const R z = ratio(x, u);
-      F0 += wf[i] * (u * L - y);
-      F1 += wf[i] * x * L;
+      F0 += w * (u * L - y);
+      F1 += w * x * L;
       zmax = fmax(zmax, fabs(z));
-      R t = wf[i] * u * z;
+      R t = w * u * z;
 #pragma unroll
       for (int k = 0; k < N - 1; ++k) {
         t *= z;
@@ -240,6 +241,7 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
       }
       Mabs += fabs(t * z);
     }
+    if (pass == 0 && amax < R(1e30) && Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
     F0 -= a0 * b;
     F1 -= b;
     if (F0 < R(0)) lo = a0; else hi = a0;
@@ -546,6 +548,15 @@ template <class Store, bool kF64Mom, int kEq = kEqSeries>
 cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const dim3 grid(static_cast<unsigned>((n + kScBlock - 1) / kScBlock), 2);
+  if constexpr (kEq == kEqEntropicAlpha) {
+    // the alpha solve keeps 2 x 81 values per thread in local memory: all of L1 for it (set on
+    // the direct launches; graphs are captured only after those)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+      e = cudaFuncSetAttribute(stream_collide_kernel<Store, kF64Mom, kEq>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (e != cudaSuccess) return e;
+  }
   stream_collide_kernel<Store, kF64Mom, kEq><<<grid, kScBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
