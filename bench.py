@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--storage", default="f32", choices=sorted(BYTES))
     p.add_argument("--equilibrium", default="series", choices=["series", "series_exact_w", "entropic"],
                    help="for --quick runs: the equilibrium of the timed case")
+    p.add_argument("--streaming", default="pingpong", choices=["pingpong", "aa"],
+                   help="for --quick runs: two buffers, or one buffer updated in place (AA)")
     p.add_argument("--collision", default="bgk", choices=["bgk", "entropic"],
                    help="for --quick runs: BGK (alpha = 2) or the entropic alpha (needs --equilibrium entropic)")
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
@@ -154,11 +156,12 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "bgk"):
+def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "bgk", streaming: str = "pingpong"):
     """DRAM bytes (read + write) of one fused-kernel launch, from the committed ncu record
     (bytes per site measured on a smaller grid, scaled by the sites; keyed by storage, plus
     "_entropic" for the exact-equilibrium kernel, "_elbm" for it with the entropic alpha and
-    "_exactw" for the series equilibrium with exact temperature weights);
+    "_exactw" for the series equilibrium with exact temperature weights, then "_aa" for in-place
+    streaming);
     None if the record is missing or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -167,7 +170,7 @@ def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "
     if rec.get("source_sha256") != kernel_source_sha():
         return None
     suffix = ("_elbm" if collision == "entropic" else "_entropic" if eq == "entropic"
-              else "_exactw" if eq == "series_exact_w" else "")
+              else "_exactw" if eq == "series_exact_w" else "") + ("_aa" if streaming == "aa" else "")
     k = rec.get("kernels", {}).get(storage + suffix)
     return None if k is None else int(round(k["dram_bytes_per_site"] * sites))
 
@@ -231,13 +234,13 @@ def time_steps(B, ctx, stream, steps: int, warmup: int, world: int, sampler=None
 
 
 def run_case(B, n: int, storage: str, steps: int, warmup: int, world: int, fp64_moments=False, sampler=None,
-             eq="series", collision="bgk"):
+             eq="series", collision="bgk", streaming="pingpong"):
     """Creates a TGV n^3 context, times `steps` steps; returns a dict of measurements."""
     import torch
     from paper_2409_05114_gb300 import workloads as W
     stream = torch.cuda.Stream()
     cfg = B.make_config(n, n, n, 0.51 - 0.5, storage, fp64_moments=fp64_moments, stream=stream, equilibrium=eq,
-                        collision=collision)
+                        collision=collision, streaming=streaming)
     ctx = B.lbm_create(cfg)
     try:
         rho, u, th = tgv_fields_device(n)
@@ -403,7 +406,7 @@ def ours(args):
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(gpu_index_for_smi(local))
     head = run_case(B, args.n, args.storage, args.steps, args.warmup, world, sampler=sampler, eq=args.equilibrium,
-                    collision=args.collision)
+                    collision=args.collision, streaming=args.streaming)
     value = head["mlups"] * world
     achieved = head["gbs"]
     line = {
@@ -414,10 +417,12 @@ def ours(args):
         "data": "synthetic (compressible Taylor-Green vortex, Ma 0.5)",
         "config": {"workload": f"taylor_green_{args.n}^3", "sites": head["sites"], "storage": args.storage,
                    "equilibrium": args.equilibrium, "collision": args.collision,
-                   "streaming": "pull, ping-pong", "tau_lb": 0.51, "parallelism": f"replicas x{world}",
+                   "streaming": "pull, ping-pong" if args.streaming == "pingpong" else "AA (one buffer, in place)",
+                   "tau_lb": 0.51, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (one step moves %.0f GB)" % (head["bytes_per_site"] * head["sites"] / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"], args.equilibrium, args.collision),
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"], args.equilibrium, args.collision,
+                                                                 args.streaming),
                      "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                      "bytes_per_site": head["bytes_per_site"]},
         "gpu_launches": head["launches"],
@@ -425,20 +430,24 @@ def ours(args):
     }
     if not args.quick and rank == 0:
         variants = {}
-        for name, n, st, mom, eq, col in (("tgv128_f32", 128, "f32", False, "series", "bgk"),
-                                          ("tgv128_f64", 128, "f64", False, "series", "bgk"),
-                                          ("tgv512_f16", 512, "f16", False, "series", "bgk"),
-                                          ("tgv512_bf16", 512, "bf16", False, "series", "bgk"),
-                                          ("tgv512_f32_fp64moments", 512, "f32", True, "series", "bgk"),
-                                          ("tgv512_f32_exactw", 512, "f32", False, "series_exact_w", "bgk"),
-                                          ("tgv512_f32_entropic", 512, "f32", False, "entropic", "bgk"),
-                                          ("tgv512_f16_entropic", 512, "f16", False, "entropic", "bgk"),
-                                          ("tgv128_f64_entropic", 128, "f64", False, "entropic", "bgk"),
-                                          ("tgv512_f32_elbm", 512, "f32", False, "entropic", "entropic"),
-                                          ("tgv512_f16_elbm", 512, "f16", False, "entropic", "entropic")):
-            if n == args.n and st == args.storage and not mom and eq == "series":
+        for name, n, st, mom, eq, col, strm in (("tgv128_f32", 128, "f32", False, "series", "bgk", "pingpong"),
+                                          ("tgv128_f64", 128, "f64", False, "series", "bgk", "pingpong"),
+                                          ("tgv512_f16", 512, "f16", False, "series", "bgk", "pingpong"),
+                                          ("tgv512_bf16", 512, "bf16", False, "series", "bgk", "pingpong"),
+                                          ("tgv512_f32_fp64moments", 512, "f32", True, "series", "bgk", "pingpong"),
+                                          ("tgv512_f32_exactw", 512, "f32", False, "series_exact_w", "bgk", "pingpong"),
+                                          ("tgv512_f32_entropic", 512, "f32", False, "entropic", "bgk", "pingpong"),
+                                          ("tgv512_f16_entropic", 512, "f16", False, "entropic", "bgk", "pingpong"),
+                                          ("tgv128_f64_entropic", 128, "f64", False, "entropic", "bgk", "pingpong"),
+                                          ("tgv512_f32_elbm", 512, "f32", False, "entropic", "entropic", "pingpong"),
+                                          ("tgv512_f16_elbm", 512, "f16", False, "entropic", "entropic", "pingpong"),
+                                          ("tgv512_f32_aa", 512, "f32", False, "series", "bgk", "aa"),
+                                          ("tgv512_f16_aa", 512, "f16", False, "series", "bgk", "aa"),
+                                          ("tgv512_f64_aa", 512, "f64", False, "series", "bgk", "aa")):
+            if n == args.n and st == args.storage and not mom and eq == "series" and strm == args.streaming:
                 continue
-            r = run_case(B, n, st, max(5, args.steps // 2), 3, 1, fp64_moments=mom, eq=eq, collision=col)
+            r = run_case(B, n, st, max(5, args.steps // 2), 3, 1, fp64_moments=mom, eq=eq, collision=col,
+                         streaming=strm)
             variants[name] = {"mlups": round(r["mlups"], 1), "gbs": round(r["gbs"], 1),
                               "roofline_frac": round(r["gbs"] / peak, 4), "ms_per_step": round(r["ms_per_step"], 4)}
         line["variants"] = variants

@@ -23,11 +23,14 @@
  * Population layout (lbm_get_populations / lbm_set_populations): dense FP64
  * f[sub][i][z][y][x], i in the library's direction order (lbm_velocities).
  *
- * Memory.  The context owns its device memory (two population buffers, ping-pong).  The
- * caller owns every field buffer it passes; the library copies in or out and keeps no
- * caller pointer after a call returns.  on_device = 1 means the pointers are device
- * pointers of the context's device (for example a torch tensor's data_ptr()), read or
- * written in order on the context's stream; on_device = 0 means host memory.
+ * Memory.  The context owns its device memory (two population buffers, ping-pong; one with
+ * AA streaming).  The caller owns every field buffer it passes; the library copies in or out
+ * and keeps no caller pointer after a call returns.  on_device = 1 means the pointers are
+ * device pointers of the context's device (for example a torch tensor's data_ptr()), read or
+ * written in order on the context's stream; on_device = 0 means host memory.  For lbm_init
+ * and lbm_moments, host fields that are page-locked and mapped (cudaHostAlloc /
+ * cudaHostRegister, e.g. pinned torch tensors; each field one allocation) are read or written
+ * in place by the kernel over the host link; pageable host memory goes through chunked copies.
  *
  * Errors.  Every call returns an lbm_status; no C++ exception crosses this interface.
  * A NULL or destroyed context gives LBM_EINVAL.  lbm_last_error() describes the last
@@ -92,6 +95,15 @@ typedef enum {
                                 positive; needs LBM_EQ_ENTROPIC */
 } lbm_collision;
 
+typedef enum {
+  LBM_STREAM_PINGPONG = 0, /* two population buffers: each step reads one and writes the other */
+  LBM_STREAM_AA = 1        /* one buffer, updated in place by two alternating step kinds: one reads and writes
+                              each site's own populations (into the slots of the opposite directions), the
+                              next pulls from and pushes to the neighbours.  Half the memory of ping-pong;
+                              the same arithmetic, so results agree with ping-pong to rounding (the step
+                              kinds are separately compiled, and a multiply-add may contract differently) */
+} lbm_streaming;
+
 typedef struct {
   int kind;                          /* lbm_bc_kind */
   double rho, ux, uy, uz, theta;     /* state of an LBM_BC_EQ_INFLOW face; ignored otherwise */
@@ -115,14 +127,16 @@ typedef struct {
   int collision;      /* lbm_collision.  LBM_COLLISION_ENTROPIC needs equilibrium =
                          LBM_EQ_ENTROPIC.  A site with a population <= 0 (where H is not
                          defined) takes alpha = 2. */
+  int streaming;      /* lbm_streaming.  LBM_STREAM_AA needs fp64_moments = 0. */
 } lbm_config;
 
 /* Device bytes lbm_create would allocate for this configuration (both population buffers
  * and internal scratch).  Returns LBM_EINVAL for an invalid configuration. */
 lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes);
 
-/* Creates a context on the current CUDA device: validates cfg, allocates two population
- * buffers.  On failure *out is NULL and lbm_last_error(NULL) tells why. */
+/* Creates a context on the current CUDA device: validates cfg, allocates the population
+ * buffers (two, or one with AA streaming).  On failure *out is NULL and lbm_last_error(NULL)
+ * tells why. */
 lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out);
 
 /* Sets every site's populations to f~eq(rho, u, theta) (App. B).  Fields as described

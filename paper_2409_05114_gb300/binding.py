@@ -26,6 +26,8 @@ LBM_EQ_SERIES, LBM_EQ_ENTROPIC, LBM_EQ_SERIES_EXACT_W = 0, 1, 2
 EQUILIBRIUM = {"series": LBM_EQ_SERIES, "entropic": LBM_EQ_ENTROPIC, "series_exact_w": LBM_EQ_SERIES_EXACT_W}
 LBM_COLLISION_BGK, LBM_COLLISION_ENTROPIC = 0, 1
 COLLISION = {"bgk": LBM_COLLISION_BGK, "entropic": LBM_COLLISION_ENTROPIC}
+LBM_STREAM_PINGPONG, LBM_STREAM_AA = 0, 1
+STREAMING = {"pingpong": LBM_STREAM_PINGPONG, "aa": LBM_STREAM_AA}
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_OFFSET, "bf16": LBM_BF16_OFFSET}
 Q = 81
 
@@ -49,7 +51,7 @@ class lbm_config(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("velset", ctypes.c_int),
                 ("tau", ctypes.c_double), ("face", lbm_bc * 6), ("storage", ctypes.c_int),
                 ("fp64_moments", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("equilibrium", ctypes.c_int),
-                ("collision", ctypes.c_int)]
+                ("collision", ctypes.c_int), ("streaming", ctypes.c_int)]
 
 
 class lbm_server_stats(ctypes.Structure):
@@ -127,17 +129,18 @@ def _ptr(a, writable: bool = False):
 
 
 def make_config(nx: int, ny: int, nz: int, tau: float, storage="f32", faces=None, fp64_moments=False,
-                stream=None, equilibrium="series", collision="bgk") -> lbm_config:
+                stream=None, equilibrium="series", collision="bgk", streaming="pingpong") -> lbm_config:
     """Builds an lbm_config.  ``faces``: up to 6 face specs (-x, +x, -y, +y, -z, +z), each
     "periodic", "zero_gradient" or ("eq_inflow", rho, ux, uy, uz, theta); default periodic.
     ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
     ``equilibrium``: "series" (App. B), "series_exact_w" (App. B with the exact weights W(theta))
     or "entropic" (Sec. III, exact).
     ``collision``: "bgk" (alpha = 2) or "entropic" (alpha from Eq. (delH); needs the entropic
-    equilibrium)."""
+    equilibrium).  ``streaming``: "pingpong" (two buffers) or "aa" (one buffer, in place)."""
     cfg = lbm_config()
     cfg.equilibrium = EQUILIBRIUM[equilibrium] if isinstance(equilibrium, str) else int(equilibrium)
     cfg.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    cfg.streaming = STREAMING[streaming] if isinstance(streaming, str) else int(streaming)
     cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
     cfg.velset = LBM_RD3Q81
     cfg.tau = float(tau)

@@ -22,7 +22,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_rd3q81.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "serve.cu", "lattice_tables.cu", "aux_kernels.cu", "sc_f64.cu", "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu", "totals_noalloc.cu", "diagnostics.cu", "selftest.cu"]
+SOURCES = ["api.cu", "serve.cu", "lattice_tables.cu", "aux_kernels.cu", "sc_f64.cu", "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu", "totals_noalloc.cu", "diagnostics.cu", "selftest.cu",
+           "sc_aa_f64.cu", "sc_aa_f32.cu", "sc_aa_f16.cu", "sc_aa_bf16.cu"]
 
 
 def nvcc() -> str:

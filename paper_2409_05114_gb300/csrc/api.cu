@@ -46,6 +46,10 @@ lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
     return *why = "equilibrium must be LBM_EQ_SERIES, LBM_EQ_ENTROPIC or LBM_EQ_SERIES_EXACT_W", LBM_EINVAL;
   if (cfg->equilibrium != LBM_EQ_SERIES && cfg->fp64_moments)
     return *why = "fp64_moments is available with the series equilibrium (LBM_EQ_SERIES) only", LBM_EINVAL;
+  if (cfg->streaming != LBM_STREAM_PINGPONG && cfg->streaming != LBM_STREAM_AA)
+    return *why = "streaming must be LBM_STREAM_PINGPONG or LBM_STREAM_AA", LBM_EINVAL;
+  if (cfg->streaming == LBM_STREAM_AA && cfg->fp64_moments)
+    return *why = "AA streaming is available with fp64_moments = 0", LBM_EINVAL;
   if (cfg->collision != LBM_COLLISION_BGK && cfg->collision != LBM_COLLISION_ENTROPIC)
     return *why = "collision must be LBM_COLLISION_BGK or LBM_COLLISION_ENTROPIC", LBM_EINVAL;
   if (cfg->collision == LBM_COLLISION_ENTROPIC && cfg->equilibrium != LBM_EQ_ENTROPIC)
@@ -100,8 +104,10 @@ struct lbm_ctx {
   int storage = 0;
   size_t elem = 0;
   long long sites = 0;  // 2 * nx * ny * nz
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
+  void* buf[2] = {nullptr, nullptr};  // AA streaming uses buf[0] only
+  int cur = 0;                        // ping-pong: the buffer holding the state
+  bool aa = false;
+  int layout = lbm::kLayoutPlain;     // StateLayout of the stored state
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -116,8 +122,10 @@ struct lbm_ctx {
   bool zero_grad[2] = {false, false};
   bool inflow[2] = {false, false};
   lbm::Feq81 feq_in[2]{};
+  lbm::Feq81 feq_in_own[2]{};  // feq_in with direction i in the slot of -c_i (AA own layout)
   long long launches = 0;
-  cudaGraphExec_t graph = nullptr;  // kGraphSteps steps starting from buffer 0
+  cudaGraphExec_t graph = nullptr;  // kGraphSteps steps starting from buffer 0 (AA: the own layout)
+  long long graph_launches = 0;     // kernel launches in one replay
   long long direct_steps = 0;       // steps issued by plain launches (the first ones load the kernels)
   std::string err = "no error";
 };
@@ -156,7 +164,21 @@ size_t aux_bytes(const lbm::Geometry& g) {
   return static_cast<size_t>(lbm::totals_blocks(g)) * 5 * sizeof(double) + 8 * sizeof(double) + 256;
 }
 
+// Device-side address of host memory p if it is page-locked and mapped into the device's
+// address space (cudaHostAlloc'd or cudaHostRegister'ed, as pinned torch tensors are): kernels
+// then read and write it directly over the host link, with no staging copies.  nullptr
+// otherwise (pageable memory goes through the chunked copies).
+void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 lbm_status fill_inflow_faces(lbm_ctx* ctx) {
+  if (ctx->aa) return LBM_OK;  // AA refills the inflow ghosts before every neighbour step
   for (int face = 0; face < 2; ++face) {
     if (!ctx->inflow[face]) continue;
     for (int b = 0; b < 2; ++b) {
@@ -186,7 +208,8 @@ lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes) {
   if (!bytes) return fail(nullptr, LBM_EINVAL, "bytes is NULL");
   if (lbm::plan_geometry(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
   const long long sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
-  *bytes = 2 * buffer_bytes(g, cfg->storage) + scratch_bytes(sites) + aux_bytes(g);
+  *bytes = (cfg->streaming == LBM_STREAM_AA ? 1 : 2) * buffer_bytes(g, cfg->storage) + scratch_bytes(sites) +
+           aux_bytes(g);
   return LBM_OK;
 }
 
@@ -235,7 +258,10 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     ctx->own_stream = true;
   }
   const size_t bb = buffer_bytes(g, ctx->storage);
-  for (int b = 0; b < 2; ++b) {
+  ctx->aa = cfg->streaming == LBM_STREAM_AA;
+  for (int face = 0; face < 2; ++face)
+    for (int i = 0; i < lbm::kQ; ++i) ctx->feq_in_own[face].v[i] = ctx->feq_in[face].v[i == 0 ? 0 : (i % 2 ? i + 1 : i - 1)];
+  for (int b = 0; b < (ctx->aa ? 1 : 2); ++b) {
     e = cudaMalloc(&ctx->buf[b], bb);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -263,10 +289,18 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
   DeviceGuard dg(ctx->device);
   const long long S = ctx->sites;
   ctx->cur = 0;
+  ctx->layout = ctx->aa ? lbm::kLayoutAAOwn : lbm::kLayoutPlain;
   LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
-  if (on_device) {
-    LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], rho, u, theta, 0,
-                                 S, S, ctx->stream, ctx->d_flag));
+  void* hr = on_device ? nullptr : mapped_host(rho);
+  void* hu = on_device ? nullptr : mapped_host(u);
+  void* ht = on_device ? nullptr : mapped_host(theta);
+  if (on_device || (hr && hu && ht)) {
+    // device fields, or pinned host fields read in place by the kernel
+    LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0],
+                                 on_device ? rho : static_cast<const double*>(hr),
+                                 on_device ? u : static_cast<const double*>(hu),
+                                 on_device ? theta : static_cast<const double*>(ht), 0, S, S, ctx->stream, ctx->d_flag,
+                                 ctx->aa ? 1 : 0));
     ++ctx->launches;
   } else {
     double* sr = ctx->d_scratch;
@@ -280,7 +314,7 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
         LBM_CK(ctx, cudaMemcpyAsync(su + a * cnt, u + a * S + first, nb, cudaMemcpyHostToDevice, ctx->stream));
       LBM_CK(ctx, cudaMemcpyAsync(st, theta + first, nb, cudaMemcpyHostToDevice, ctx->stream));
       LBM_CK(ctx, lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], sr, su, st,
-                                   first, cnt, cnt, ctx->stream, ctx->d_flag));
+                                   first, cnt, cnt, ctx->stream, ctx->d_flag, ctx->aa ? 1 : 0));
       ++ctx->launches;
     }
   }
@@ -293,38 +327,86 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
 
 namespace {
 
-// Issues one step (ghost fills + fused kernel) reading buffer `cur` on stream s.
-cudaError_t issue_step(lbm_ctx* ctx, int cur, cudaStream_t s) {
-  for (int face = 0; face < 2; ++face) {
-    if (!ctx->zero_grad[face]) continue;
-    cudaError_t e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
-    if (e != cudaSuccess) return e;
-  }
+int step_mode(const lbm_ctx* ctx) {
+  return ctx->cfg.equilibrium == LBM_EQ_ENTROPIC
+             ? (ctx->cfg.collision == LBM_COLLISION_ENTROPIC ? lbm::kEqEntropicAlpha : lbm::kEqEntropic)
+         : ctx->cfg.equilibrium == LBM_EQ_SERIES_EXACT_W ? lbm::kEqSeriesExactW
+                                                          : lbm::kEqSeries;
+}
+
+// Issues one step on stream s and adds its launches to *launches.  Ping-pong: ghost fills,
+// then the fused kernel from buffer `cur` into the other.  AA (buffer 0, in place): from the
+// own layout, ghost fills in that layout, the neighbour step, then what the ghosts push into
+// the interior (leaves the pushed layout); from the pushed layout, the own-site step.
+cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long long* launches) {
   lbm::StepParams p;
   p.g = ctx->g;
   p.omega = ctx->omega;
   p.flag = ctx->d_flag;
   p.tab = ctx->tab;
-  p.src = ctx->buf[cur];
-  p.dst = ctx->buf[cur ^ 1];
-  lbm::fill_slab_bases(&p, ctx->elem);
-  const int mode = ctx->cfg.equilibrium == LBM_EQ_ENTROPIC
-                       ? (ctx->cfg.collision == LBM_COLLISION_ENTROPIC ? lbm::kEqEntropicAlpha : lbm::kEqEntropic)
-                   : ctx->cfg.equilibrium == LBM_EQ_SERIES_EXACT_W ? lbm::kEqSeriesExactW
-                                                                    : lbm::kEqSeries;
-  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, mode, p, s);
+  cudaError_t e = cudaSuccess;
+  if (!ctx->aa) {
+    for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
+      if (!ctx->zero_grad[face]) continue;
+      e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
+      ++*launches;
+    }
+    if (e != cudaSuccess) return e;
+    p.src = ctx->buf[cur];
+    p.dst = ctx->buf[cur ^ 1];
+    lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepPingPong);
+    ++*launches;
+    return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, step_mode(ctx), lbm::kStepPingPong, p, s);
+  }
+  p.src = ctx->buf[0];
+  p.dst = ctx->buf[0];
+  if (layout == lbm::kLayoutAAPushed) {
+    lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepAAOwn);
+    ++*launches;
+    return lbm::launch_stream_collide(ctx->storage, 0, step_mode(ctx), lbm::kStepAAOwn, p, s);
+  }
+  for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
+    if (ctx->zero_grad[face]) e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, s);
+    else if (ctx->inflow[face])
+      e = lbm::launch_fill_inflow(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->feq_in_own[face], s);
+    else continue;
+    ++*launches;
+  }
+  if (e != cudaSuccess) return e;
+  lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepAANeighbour);
+  ++*launches;
+  e = lbm::launch_stream_collide(ctx->storage, 0, step_mode(ctx), lbm::kStepAANeighbour, p, s);
+  for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
+    if (!ctx->zero_grad[face] && !ctx->inflow[face]) continue;
+    e = lbm::launch_aa_ghost_push(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->zero_grad[face] ? 1 : 0,
+                                  ctx->feq_in[face], s);
+    ++*launches;
+  }
+  return e;
 }
 
-int launches_per_step(const lbm_ctx* ctx) { return 1 + (ctx->zero_grad[0] ? 1 : 0) + (ctx->zero_grad[1] ? 1 : 0); }
+// The state after one step: ping-pong flips the buffer; AA flips the layout.
+void advance(lbm_ctx* ctx) {
+  if (ctx->aa)
+    ctx->layout = ctx->layout == lbm::kLayoutAAOwn ? lbm::kLayoutAAPushed : lbm::kLayoutAAOwn;
+  else
+    ctx->cur ^= 1;
+}
 
-// Captures kGraphSteps steps starting from buffer 0 (the ping-pong returns to buffer 0).
+// True when the state is where a captured run starts: buffer 0 (ping-pong) or the AA own layout.
+bool at_graph_start(const lbm_ctx* ctx) { return ctx->aa ? ctx->layout == lbm::kLayoutAAOwn : ctx->cur == 0; }
+
+// Captures kGraphSteps steps starting from buffer 0 / the AA own layout (an even number of
+// steps returns there).
 cudaError_t build_graph(lbm_ctx* ctx) {
   cudaStream_t cap;
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return e;
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  for (int k = 0; e == cudaSuccess && k < kGraphSteps; ++k) e = issue_step(ctx, k & 1, cap);
+  ctx->graph_launches = 0;
+  for (int k = 0; e == cudaSuccess && k < kGraphSteps; ++k)
+    e = issue_step(ctx, k & 1, (k & 1) ? lbm::kLayoutAAPushed : lbm::kLayoutAAOwn, cap, &ctx->graph_launches);
   cudaError_t e2 = cudaStreamEndCapture(cap, &g);
   if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
@@ -353,24 +435,22 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n) {
   if (graphs) {
     // plain steps first: until two have run (kernels loaded before any capture) and until
     // the state is back in buffer 0, where the graph starts
-    while (ctx->direct_steps < 2 || ctx->cur == 1) {
-      LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->stream));
-      ctx->launches += launches_per_step(ctx);
+    while (ctx->direct_steps < 2 || !at_graph_start(ctx)) {
+      LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->layout, ctx->stream, &ctx->launches));
       ++ctx->direct_steps;
-      ctx->cur ^= 1;
+      advance(ctx);
       ++k;
     }
     if (!ctx->graph && n - k >= kGraphSteps) LBM_CK(ctx, build_graph(ctx));
     for (; n - k >= kGraphSteps; k += kGraphSteps) {
       LBM_CK(ctx, cudaGraphLaunch(ctx->graph, ctx->stream));
-      ctx->launches += static_cast<long long>(kGraphSteps) * launches_per_step(ctx);
+      ctx->launches += ctx->graph_launches;
     }
   }
   for (; k < n; ++k) {
-    LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->stream));
-    ctx->launches += launches_per_step(ctx);
+    LBM_CK(ctx, issue_step(ctx, ctx->cur, ctx->layout, ctx->stream, &ctx->launches));
     ++ctx->direct_steps;
-    ctx->cur ^= 1;
+    advance(ctx);
   }
   return LBM_OK;
 }
@@ -382,8 +462,14 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int 
   DeviceGuard dg(ctx->device);
   const long long S = ctx->sites;
   const void* b = ctx->buf[ctx->cur];
-  if (on_device) {
-    LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, rho, u, theta, 0, S, S, ctx->stream));
+  void* hr = on_device ? nullptr : mapped_host(rho);
+  void* hu = on_device ? nullptr : mapped_host(u);
+  void* ht = on_device ? nullptr : mapped_host(theta);
+  if (on_device || (hr && hu && ht)) {
+    // device fields, or pinned host fields written in place by the kernel
+    LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, on_device ? rho : static_cast<double*>(hr),
+                                    on_device ? u : static_cast<double*>(hu),
+                                    on_device ? theta : static_cast<double*>(ht), 0, S, S, ctx->stream, ctx->layout));
     ++ctx->launches;
   } else {
     double* sr = ctx->d_scratch;
@@ -392,7 +478,8 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int 
     for (long long first = 0; first < S; first += ctx->chunk) {
       const long long cnt = S - first < ctx->chunk ? S - first : ctx->chunk;
       const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
-      LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, sr, su, st, first, cnt, cnt, ctx->stream));
+      LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, sr, su, st, first, cnt, cnt, ctx->stream,
+                                      ctx->layout));
       ++ctx->launches;
       LBM_CK(ctx, cudaMemcpyAsync(rho + first, sr, nb, cudaMemcpyDeviceToHost, ctx->stream));
       for (int a = 0; a < 3; ++a)
@@ -409,7 +496,7 @@ lbm_status lbm_totals(lbm_ctx* ctx, double* out5) {
   if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
   DeviceGuard dg(ctx->device);
   LBM_CK(ctx, lbm::launch_totals(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], ctx->d_partials,
-                                 ctx->totals_nb, ctx->d_totals, ctx->stream));
+                                 ctx->totals_nb, ctx->d_totals, ctx->stream, ctx->layout));
   ctx->launches += 2;
   LBM_CK(ctx, cudaMemcpyAsync(out5, ctx->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   LBM_CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -437,7 +524,7 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, double* out2) {
   double* partials = theta + S;
   double* dout = partials + 2 * nb;
   cudaError_t e = lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], rho, u, theta, 0, S, S,
-                                      ctx->stream);
+                                      ctx->stream, ctx->layout);
   if (e == cudaSuccess) e = lbm::launch_diagnostics(ctx->g, rho, u, S, partials, dout, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out2, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   ctx->launches += 3;
@@ -455,14 +542,14 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, double* f, int on_device) {
   const long long total = ctx->sites * lbm::kQ;
   const void* b = ctx->buf[ctx->cur];
   if (on_device) {
-    LBM_CK(ctx, lbm::launch_get_populations(ctx->storage, ctx->g, ctx->tab, b, f, 0, total, ctx->stream));
+    LBM_CK(ctx, lbm::launch_get_populations(ctx->storage, ctx->g, ctx->tab, b, f, 0, total, ctx->stream, ctx->layout));
     ++ctx->launches;
   } else {
     const long long ck = 5 * ctx->chunk;
     for (long long first = 0; first < total; first += ck) {
       const long long cnt = total - first < ck ? total - first : ck;
       LBM_CK(ctx, lbm::launch_get_populations(ctx->storage, ctx->g, ctx->tab, b, ctx->d_scratch, first, cnt,
-                                              ctx->stream));
+                                              ctx->stream, ctx->layout));
       ++ctx->launches;
       LBM_CK(ctx, cudaMemcpyAsync(f + first, ctx->d_scratch, static_cast<size_t>(cnt) * sizeof(double),
                                   cudaMemcpyDeviceToHost, ctx->stream));
@@ -478,8 +565,10 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, int on_device) {
   DeviceGuard dg(ctx->device);
   const long long total = ctx->sites * lbm::kQ;
   ctx->cur = 0;
+  ctx->layout = ctx->aa ? lbm::kLayoutAAOwn : lbm::kLayoutPlain;
   if (on_device) {
-    LBM_CK(ctx, lbm::launch_set_populations(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], f, 0, total, ctx->stream));
+    LBM_CK(ctx, lbm::launch_set_populations(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], f, 0, total, ctx->stream,
+                                            ctx->layout));
     ++ctx->launches;
   } else {
     const long long ck = 5 * ctx->chunk;
@@ -488,7 +577,7 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, const double* f, int on_device) {
       LBM_CK(ctx, cudaMemcpyAsync(ctx->d_scratch, f + first, static_cast<size_t>(cnt) * sizeof(double),
                                   cudaMemcpyHostToDevice, ctx->stream));
       LBM_CK(ctx, lbm::launch_set_populations(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], ctx->d_scratch, first,
-                                              cnt, ctx->stream));
+                                              cnt, ctx->stream, ctx->layout));
       ++ctx->launches;
     }
   }
@@ -516,7 +605,7 @@ lbm_status lbm_probe(lbm_ctx* ctx, const long long* sites, long long count, doub
     LBM_CK(ctx, cudaMemcpyAsync(d_sites, sites + first, cnt * sizeof(long long), cudaMemcpyHostToDevice,
                                 ctx->stream));
     LBM_CK(ctx, lbm::launch_probe(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], d_sites, cnt, d_vals,
-                                  ctx->stream));
+                                  ctx->stream, ctx->layout));
     ++ctx->launches;
     LBM_CK(ctx, cudaMemcpyAsync(f + first * lbm::kQ, d_vals, cnt * lbm::kQ * sizeof(double),
                                 cudaMemcpyDeviceToHost, ctx->stream));

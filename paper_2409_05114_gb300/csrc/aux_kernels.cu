@@ -18,6 +18,26 @@ __device__ __forceinline__ long long site_offset(const Geometry& g, int sub, lon
   return sub * g.sub_stride + z * g.plane + static_cast<long long>(y) * g.pitch + g.xoff + x;
 }
 
+// Element offset of population i of interior site t of sublattice sub in the stored state
+// (StateLayout): own slot, the slot of -c_i (AA own), or slot i of the site that pulls it
+// next (AA pushed; on a non-periodic x face that site may be a ghost).
+__device__ __forceinline__ long long pop_offset(const Geometry& g, const LatticeTables& tab, int layout, int sub,
+                                                long long t, int i) {
+  const int x = static_cast<int>(t % g.nx);
+  const long long r = t / g.nx;
+  const int y = static_cast<int>(r % g.ny);
+  const int z = static_cast<int>(r / g.ny);
+  if (layout == kLayoutAAPushed) {
+    const signed char* d = tab.push_d[sub][i];
+    const int xx = g.x_periodic ? wrap_idx(x - d[0], g.nx) : x - d[0];
+    const int yy = wrap_idx(y - d[1], g.ny), zz = wrap_idx(z - d[2], g.nz);
+    return d[3] * g.sub_stride + zz * g.plane + static_cast<long long>(yy) * g.pitch + g.xoff + xx +
+           i * g.dir_stride;
+  }
+  const int slot = layout == kLayoutAAOwn ? tab.opp[i] : i;
+  return sub * g.sub_stride + z * g.plane + static_cast<long long>(y) * g.pitch + g.xoff + x + slot * g.dir_stride;
+}
+
 template <class S>
 __device__ __forceinline__ double decode(S v, double w) {
   if constexpr (Codec<S>::kOffset) {
@@ -39,7 +59,7 @@ __device__ __forceinline__ void encode(S* p, double f, double w) {
 template <class S, int kEq>
 __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double* rho, const double* u,
                             const double* theta, long long first, long long count, long long us,
-                            unsigned int* flag) {
+                            unsigned int* flag, int own_slots) {
   const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
   if (k >= count) return;
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
@@ -63,10 +83,12 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
   }
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
+    constexpr int io = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
+    S* q = buf + off + (own_slots ? io : i) * g.dir_stride;  // AA keeps f_i in the slot of -c_i
     if constexpr (Codec<S>::kOffset)
-      Codec<S>::store(buf + off + i * g.dir_stride, feq[i] - R(1));
+      Codec<S>::store(q, feq[i] - R(1));
     else
-      Codec<S>::store(buf + off + i * g.dir_stride, feq[i]);
+      Codec<S>::store(q, feq[i]);
   });
 }
 
@@ -76,9 +98,10 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
 // one magnitude class, exact to the storage's own precision), and the 11 shell sums are
 // combined in FP64: FP64-quality moments at a tenth of the FP64 operations.
 template <class S>
-__device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTables& tab, const S* buf,
-                                             long long off, double& rho, double& jx, double& jy,
+__device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTables& tab, const S* buf, int layout,
+                                             int sub, long long t, double& rho, double& jx, double& jy,
                                              double& jz, double& e) {
+  const long long off = site_offset(g, sub, t);
   using R = typename Codec<S>::Real;
   R sr[kShells], sx[kShells], sy[kShells], sz[kShells];
 #pragma unroll
@@ -86,7 +109,8 @@ __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTab
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
-    const R f = Codec<S>::load(buf + off + i * g.dir_stride);
+    const R f = Codec<S>::load(buf + (layout == kLayoutPlain ? off + i * g.dir_stride
+                                                             : pop_offset(g, tab, layout, sub, t, i)));
     sr[d.shell] += f;
     if constexpr (d.hx != 0) sx[d.shell] += R(0.5 * d.hx) * f;
     if constexpr (d.hy != 0) sy[d.shell] += R(0.5 * d.hy) * f;
@@ -110,7 +134,7 @@ __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTab
 }
 
 template <class S>
-__global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, double* rho, double* u,
+__global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, int layout, double* rho, double* u,
                                double* theta, long long first, long long count, long long us) {
   const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
   if (k >= count) return;
@@ -118,7 +142,7 @@ __global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, doub
   const long long gs = first + k;
   const int sub = gs >= n ? 1 : 0;
   double r, jx, jy, jz, e;
-  site_moments<S>(g, tab, buf, site_offset(g, sub, gs - sub * n), r, jx, jy, jz, e);
+  site_moments<S>(g, tab, buf, layout, sub, gs - sub * n, r, jx, jy, jz, e);
   const double ux = jx / r, uy = jy / r, uz = jz / r;
   rho[k] = r;
   u[k] = ux;
@@ -131,7 +155,7 @@ __global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, doub
 // Dense element k = (sub*81 + i)*n + t; the kernels handle k in [first, first + count)
 // with f pointing at element `first`.
 template <class S>
-__global__ void get_pop_kernel(Geometry g, LatticeTables tab, const S* buf, double* f, long long first,
+__global__ void get_pop_kernel(Geometry g, LatticeTables tab, const S* buf, int layout, double* f, long long first,
                                long long count) {
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
   const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
@@ -140,11 +164,11 @@ __global__ void get_pop_kernel(Geometry g, LatticeTables tab, const S* buf, doub
   const long long t = k % n;
   const int i = static_cast<int>((k / n) % kQ);
   const int sub = static_cast<int>(k / (n * kQ));
-  f[j] = decode<S>(buf[site_offset(g, sub, t) + i * g.dir_stride], tab.wdir[i]);
+  f[j] = decode<S>(buf[pop_offset(g, tab, layout, sub, t, i)], tab.wdir[i]);
 }
 
 template <class S>
-__global__ void set_pop_kernel(Geometry g, LatticeTables tab, S* buf, const double* f, long long first,
+__global__ void set_pop_kernel(Geometry g, LatticeTables tab, S* buf, int layout, const double* f, long long first,
                                long long count) {
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
   const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
@@ -153,12 +177,12 @@ __global__ void set_pop_kernel(Geometry g, LatticeTables tab, S* buf, const doub
   const long long t = k % n;
   const int i = static_cast<int>((k / n) % kQ);
   const int sub = static_cast<int>(k / (n * kQ));
-  encode<S>(buf + site_offset(g, sub, t) + i * g.dir_stride, f[j], tab.wdir[i]);
+  encode<S>(buf + pop_offset(g, tab, layout, sub, t, i), f[j], tab.wdir[i]);
 }
 
 // Populations of selected sites: thread per (sample, direction).
 template <class S>
-__global__ void probe_kernel(Geometry g, LatticeTables tab, const S* buf, const long long* sites,
+__global__ void probe_kernel(Geometry g, LatticeTables tab, const S* buf, int layout, const long long* sites,
                              long long count, double* f) {
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
   const long long j = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
@@ -167,7 +191,7 @@ __global__ void probe_kernel(Geometry g, LatticeTables tab, const S* buf, const 
   const int i = static_cast<int>(j % kQ);
   const long long gs = sites[k];
   const int sub = gs >= n ? 1 : 0;
-  f[j] = decode<S>(buf[site_offset(g, sub, gs - sub * n) + i * g.dir_stride], tab.wdir[i]);
+  f[j] = decode<S>(buf[pop_offset(g, tab, layout, sub, gs - sub * n, i)], tab.wdir[i]);
 }
 
 // Ghost layers of one x face: thread per (sub, i, z, y) row.  Zero gradient copies the
@@ -208,18 +232,59 @@ __global__ void inflow_kernel(Geometry g, LatticeTables tab, S* buf, int face, F
   for (int l = 0; l < rd3q81::kReach; ++l) encode<S>(buf + row + x0 + l, feq.v[i], tab.wdir[i]);
 }
 
+// AA streaming, after a neighbour step: the populations a ghost site of this x face would have
+// pushed into the interior (the neighbour step runs on interior sites only).  Thread per
+// (sub, z, y, ghost layer).  Zero gradient: the ghost holds the nearest interior site's
+// post-collision populations, which that site pushed to the same relative place; inflow: feq.
+template <class S>
+__global__ void aa_ghost_push_kernel(Geometry g, LatticeTables tab, S* buf, int face, int zero_grad, Feq81 feq) {
+  const long long cols = 2LL * g.nz * g.ny * rd3q81::kReach;
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= cols) return;
+  const int l = static_cast<int>(k % rd3q81::kReach);
+  long long r = k / rd3q81::kReach;
+  const int y = static_cast<int>(r % g.ny);
+  r /= g.ny;
+  const int z = static_cast<int>(r % g.nz);
+  const int sub = static_cast<int>(r / g.nz);
+  const int gx = face == 0 ? -1 - l : g.nx + l;
+  const int xn = face == 0 ? 0 : g.nx - 1;
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[i];
+    if constexpr (d.hx != 0) {
+      if ((face == 0) == (d.hx > 0)) {  // enters the interior through this face
+        const int pdx = sub == 0 ? rd3q81::pull_disp(-d.hx, 0) : rd3q81::pull_disp(-d.hx, 1);
+        const int pdy = sub == 0 ? rd3q81::pull_disp(-d.hy, 0) : rd3q81::pull_disp(-d.hy, 1);
+        const int pdz = sub == 0 ? rd3q81::pull_disp(-d.hz, 0) : rd3q81::pull_disp(-d.hz, 1);
+        const int to = (d.hx % 2 != 0) ? 1 - sub : sub;
+        const int tx = gx - pdx;
+        if (tx >= 0 && tx < g.nx) {
+          const int ty = wrap_idx(y - pdy, g.ny), tz = wrap_idx(z - pdz, g.nz);
+          const long long base = to * g.sub_stride + tz * g.plane + static_cast<long long>(ty) * g.pitch + g.xoff +
+                                 i * g.dir_stride;
+          if (zero_grad)
+            buf[base + tx] = buf[base + (xn - pdx)];
+          else
+            encode<S>(buf + base + tx, feq.v[i], tab.wdir[i]);
+        }
+      }
+    }
+  });
+}
+
 // Global sums (rho, j_x, j_y, j_z, <f, c^2>) over all sites.  Pass 1: per-block partials
 // (fixed grid, fixed per-thread order); pass 2: one block sums them in a fixed order, so
 // the result is bitwise reproducible.
 template <class S>
-__global__ void totals_pass1(Geometry g, LatticeTables tab, const S* buf, double* partials) {
+__global__ void totals_pass1(Geometry g, LatticeTables tab, const S* buf, int layout, double* partials) {
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
   double acc[5] = {0, 0, 0, 0, 0};
   for (long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x; k < 2 * n;
        k += static_cast<long long>(gridDim.x) * kAuxBlock) {
     const int sub = k >= n ? 1 : 0;
     double r, jx, jy, jz, e;
-    site_moments<S>(g, tab, buf, site_offset(g, sub, k - sub * n), r, jx, jy, jz, e);
+    site_moments<S>(g, tab, buf, layout, sub, k - sub * n, r, jx, jy, jz, e);
     acc[0] += r;
     acc[1] += jx;
     acc[2] += jy;
@@ -261,44 +326,49 @@ unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kAuxBlock -
 cudaError_t launch_init(int storage, int eq, const Geometry& g, const LatticeTables& tab, void* buf,
                         const double* rho, const double* u, const double* theta,
                         long long first_site, long long count, long long u_stride, cudaStream_t s,
-                        unsigned int* flag) {
+                        unsigned int* flag, int own_slots) {
   if (count <= 0) return cudaSuccess;
   if (eq == 1) {
     LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 1><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag,
+                                      own_slots)));
   } else if (eq == 2) {
     LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 2><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag,
+                                      own_slots)));
   } else {
     LBM_STORAGE_DISPATCH(storage, (init_kernel<S, 0><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag)));
+                                      g, tab, static_cast<S*>(buf), rho, u, theta, first_site, count, u_stride, flag,
+                                      own_slots)));
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
                            double* rho, double* u, double* theta, long long first_site,
-                           long long count, long long u_stride, cudaStream_t s) {
+                           long long count, long long u_stride, cudaStream_t s, int layout) {
   if (count <= 0) return cudaSuccess;
   LBM_STORAGE_DISPATCH(storage, (moments_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<const S*>(buf), rho, u, theta, first_site, count, u_stride)));
+                                    g, tab, static_cast<const S*>(buf), layout, rho, u, theta, first_site, count,
+                                    u_stride)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_populations(int storage, const Geometry& g, const LatticeTables& tab,
                                    const void* buf, double* f, long long first, long long count,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int layout) {
   if (count <= 0) return cudaSuccess;
   LBM_STORAGE_DISPATCH(storage, (get_pop_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<const S*>(buf), f, first, count)));
+                                    g, tab, static_cast<const S*>(buf), layout, f, first, count)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_populations(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
-                                   const double* f, long long first, long long count, cudaStream_t s) {
+                                   const double* f, long long first, long long count, cudaStream_t s,
+                                   int layout) {
   if (count <= 0) return cudaSuccess;
   LBM_STORAGE_DISPATCH(storage, (set_pop_kernel<S><<<blocks_for(count), kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<S*>(buf), f, first, count)));
+                                    g, tab, static_cast<S*>(buf), layout, f, first, count)));
   return cudaGetLastError();
 }
 
@@ -318,10 +388,10 @@ cudaError_t launch_fill_inflow(int storage, const Geometry& g, const LatticeTabl
 }
 
 cudaError_t launch_probe(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
-                         const long long* sites, long long count, double* f, cudaStream_t s) {
+                         const long long* sites, long long count, double* f, cudaStream_t s, int layout) {
   if (count <= 0) return cudaSuccess;
   LBM_STORAGE_DISPATCH(storage, (probe_kernel<S><<<blocks_for(count * kQ), kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<const S*>(buf), sites, count, f)));
+                                    g, tab, static_cast<const S*>(buf), layout, sites, count, f)));
   return cudaGetLastError();
 }
 
@@ -332,16 +402,35 @@ int totals_blocks(const Geometry& g) {
 }
 
 cudaError_t launch_totals(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
-                          double* partials, int nblocks, double* out5, cudaStream_t s) {
+                          double* partials, int nblocks, double* out5, cudaStream_t s, int layout) {
   LBM_STORAGE_DISPATCH(storage, (totals_pass1<S><<<nblocks, kAuxBlock, 0, s>>>(
-                                    g, tab, static_cast<const S*>(buf), partials)));
+                                    g, tab, static_cast<const S*>(buf), layout, partials)));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   totals_pass2<<<1, 32, 0, s>>>(partials, nblocks, out5);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, const StepParams& p, cudaStream_t s) {
+cudaError_t launch_aa_ghost_push(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
+                                 int zero_grad, const Feq81& feq, cudaStream_t s) {
+  const long long cols = 2LL * g.nz * g.ny * rd3q81::kReach;
+  LBM_STORAGE_DISPATCH(storage, (aa_ghost_push_kernel<S><<<blocks_for(cols), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<S*>(buf), face, zero_grad, feq)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, int kind, const StepParams& p,
+                                  cudaStream_t s) {
+  if (kind != kStepPingPong) {
+    if (fp64_moments) return cudaErrorInvalidValue;
+    switch (storage) {
+      case kF64: return launch_sc_aa_f64(eq, kind, p, s);
+      case kF32: return launch_sc_aa_f32(eq, kind, p, s);
+      case kF16Off: return launch_sc_aa_f16(eq, kind, p, s);
+      case kBF16Off: return launch_sc_aa_bf16(eq, kind, p, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (storage) {
     case kF64: return launch_sc_f64(fp64_moments, eq, p, s);
     case kF32: return launch_sc_f32(fp64_moments, eq, p, s);

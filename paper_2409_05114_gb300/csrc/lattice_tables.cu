@@ -65,16 +65,37 @@ void build_lattice_tables(LatticeTables* t) {
   }
   t->theta0f = static_cast<float>(t0);
   for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
+  for (int i = 0; i < kQ; ++i) {
+    t->opp[i] = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
+    const Dir& d = kDirs[i];
+    for (int s = 0; s < 2; ++s) {
+      // the site that pulls f_i from (s, n) is the source of -c_i at (s, n)
+      t->push_d[s][i][0] = static_cast<signed char>(pull_disp(-d.hx, s));
+      t->push_d[s][i][1] = static_cast<signed char>(pull_disp(-d.hy, s));
+      t->push_d[s][i][2] = static_cast<signed char>(pull_disp(-d.hz, s));
+      t->push_d[s][i][3] = static_cast<signed char>(d.hx % 2 != 0 ? 1 - s : s);
+    }
+  }
 }
 
-void fill_slab_bases(StepParams* p, size_t elem) {
+void fill_slab_bases(StepParams* p, size_t elem, int kind) {
   const char* src = static_cast<const char*>(p->src);
   char* dst = static_cast<char*>(p->dst);
+  const long long e = static_cast<long long>(elem);
   for (int sub = 0; sub < 2; ++sub)
     for (int i = 0; i < kQ; ++i) {
-      const int from = (rd3q81::kDirs[i].hx % 2 != 0) ? 1 - sub : sub;
-      p->src_slab[sub][i] = src + (from * p->g.sub_stride + i * p->g.dir_stride) * static_cast<long long>(elem);
-      p->dst_slab[sub][i] = dst + (sub * p->g.sub_stride + i * p->g.dir_stride) * static_cast<long long>(elem);
+      const int other = (rd3q81::kDirs[i].hx % 2 != 0) ? 1 - sub : sub;  // sublattice across link i
+      const int opp = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
+      int ls = other, li = i, ss = sub, si = i;  // load sublattice / slot, store sublattice / slot
+      if (kind == kStepAANeighbour) {
+        li = opp;    // the neighbour left f_i in its slot of -c_i
+        ss = other;  // and f_i goes to the neighbour that pulls it, slot i
+      } else if (kind == kStepAAOwn) {
+        ls = sub;    // own site, slot i (pushed there by the neighbour step)
+        si = opp;    // own site, slot of -c_i
+      }
+      p->src_slab[sub][i] = src + (ls * p->g.sub_stride + li * p->g.dir_stride) * e;
+      p->dst_slab[sub][i] = dst + (ss * p->g.sub_stride + si * p->g.dir_stride) * e;
     }
 }
 

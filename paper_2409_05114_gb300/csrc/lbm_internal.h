@@ -41,7 +41,21 @@ struct LatticeTables {
   float naf[5], nbf[5];
   float theta0f;
   double wdir[kQ];  // w_i per direction (decoding offset storage in the auxiliary kernels)
+  // In-place (AA) streaming: opp[i] = index of -c_i; the site that pulls f_i from site n of
+  // sublattice s is n - push_d[s][i][0..2] on sublattice push_d[s][i][3].
+  int opp[kQ];
+  signed char push_d[2][kQ][4];
 };
+
+// Where the stored state keeps population i of site (s, n):
+//   kLayoutPlain    (ping-pong)                           at (s, n), slot i;
+//   kLayoutAAOwn    (AA, after init or an own-site step)  at (s, n), slot opp[i];
+//   kLayoutAAPushed (AA, after a neighbour step)          at the site that pulls it, slot i.
+enum StateLayout { kLayoutPlain = 0, kLayoutAAOwn = 1, kLayoutAAPushed = 2 };
+// Kinds of step: ping-pong; AA from the own layout (pulls from the neighbours' opp slots and
+// pushes into their slots: leaves kLayoutAAPushed); AA from the pushed layout (reads and
+// writes its own site: leaves kLayoutAAOwn).
+enum StepKind { kStepPingPong = 0, kStepAANeighbour = 1, kStepAAOwn = 2 };
 
 // Builds the tables (host, FP64).  Defined in lattice_tables.cu.
 void build_lattice_tables(LatticeTables* t);
@@ -74,8 +88,9 @@ struct StepParams {
   void* dst_slab[2][kQ];
 };
 
-// Fills p.src_slab / p.dst_slab from p.src, p.dst, p.g and the element size.
-void fill_slab_bases(StepParams* p, size_t elem);
+// Fills p.src_slab / p.dst_slab from p.src, p.dst, p.g and the element size, for a step of
+// the given kind (StepKind; the AA kinds use p.src == p.dst).
+void fill_slab_bases(StepParams* p, size_t elem, int kind = kStepPingPong);
 
 // Validates cfg and derives its buffer geometry (api.cu); LBM_OK or LBM_EINVAL with *why.
 lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why);
@@ -126,33 +141,43 @@ inline size_t storage_bytes(int s) { return s == kF64 ? 8 : s == kF32 ? 4 : 2; }
 // eq: kEqSeries (App. B equilibrium, BGK), kEqSeriesExactW (the same with the exact
 // temperature weights of Eq. (zeroveleq)), kEqEntropic (exact entropic equilibrium of Sec. III,
 // BGK) or kEqEntropicAlpha (exact entropic equilibrium, entropic alpha of Eq. (delH)).
-cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+// kind: StepKind (AA kinds in the sc_aa_*.cu units; they take fp64_moments = 0).
+cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f64(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f32(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_bf16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f64(int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f32(int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f16(int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_bf16(int eq, int kind, const StepParams& p, cudaStream_t s);
 
-// Auxiliary kernels (aux_kernels.cu).
+// Auxiliary kernels (aux_kernels.cu).  `layout` (StateLayout) says where the stored state
+// keeps each population; own_slots = 1 writes the initial state in the AA own layout.
 cudaError_t launch_init(int storage, int eq, const Geometry& g, const LatticeTables& tab, void* buf,
                         const double* rho, const double* u, const double* theta,
                         long long first_site, long long count, long long u_stride, cudaStream_t s,
-                        unsigned int* flag);
+                        unsigned int* flag, int own_slots = 0);
 struct Feq81 {
   double v[kQ];
 };
 cudaError_t launch_fill_inflow(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
                                int face, const Feq81& feq, cudaStream_t s);
 cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s);
+// AA: after a neighbour step, what the ghost sites of one x face push into the interior.
+cudaError_t launch_aa_ghost_push(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
+                                 int zero_grad, const Feq81& feq, cudaStream_t s);
 cudaError_t launch_moments(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
                            double* rho, double* u, double* theta, long long first_site,
-                           long long count, long long u_stride, cudaStream_t s);
+                           long long count, long long u_stride, cudaStream_t s, int layout = kLayoutPlain);
 cudaError_t launch_get_populations(int storage, const Geometry& g, const LatticeTables& tab,
                                    const void* buf, double* f, long long first, long long count,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int layout = kLayoutPlain);
 cudaError_t launch_set_populations(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
-                                   const double* f, long long first, long long count, cudaStream_t s);
+                                   const double* f, long long first, long long count, cudaStream_t s,
+                                   int layout = kLayoutPlain);
 cudaError_t launch_totals(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
-                          double* partials, int nblocks, double* out5, cudaStream_t s);
+                          double* partials, int nblocks, double* out5, cudaStream_t s, int layout = kLayoutPlain);
 
 // Mean kinetic energy and enstrophy (Sec. IV C) from FP64 fields rho[sites], u[3][sites] (sites
 // ordered sub, z, y, x); partials holds 2 * diagnostics_blocks(sites) doubles; out2 (device) gets
@@ -162,7 +187,8 @@ cudaError_t launch_diagnostics(const Geometry& g, const double* rho, const doubl
                                double* partials, double* out2, cudaStream_t s);
 int totals_blocks(const Geometry& g);
 cudaError_t launch_probe(int storage, const Geometry& g, const LatticeTables& tab, const void* buf,
-                         const long long* sites, long long count, double* f, cudaStream_t s);
+                         const long long* sites, long long count, double* f, cudaStream_t s,
+                         int layout = kLayoutPlain);
 
 // The App. B equilibrium of one state in FP64 (host and device) is equilibrium_f64() in
 // device_common.cuh; init and the inflow faces use it.

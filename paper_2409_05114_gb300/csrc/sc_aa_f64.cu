@@ -1,0 +1,12 @@
+// Fused stream-collide instantiations for double storage with in-place (AA) streaming: both step
+// kinds for every equilibrium and collision (own translation unit so that it compiles in
+// parallel with the ping-pong one).
+#include "stream_collide.cuh"
+
+namespace lbm {
+
+cudaError_t launch_sc_aa_f64(int eq, int kind, const StepParams& p, cudaStream_t s) {
+  return launch_sc_aa_all<double>(eq, kind, p, s);
+}
+
+}  // namespace lbm

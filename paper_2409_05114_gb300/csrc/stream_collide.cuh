@@ -497,8 +497,13 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
 }
 
 // The single-case form of site_update: the same phases, with the slab base addresses taken
-// from the kernel parameters instead of being computed per access.
-template <class Store, bool kF64Mom, int SUB, int kEq>
+// from the kernel parameters instead of being computed per access.  kKind (StepKind) picks
+// where population i is read and written; the slab bases (fill_slab_bases) pick the
+// sublattice and slot:
+//   ping-pong:    read the source of c_i (pull),  write own site;
+//   AA neighbour: read the source of c_i (pull),  write the site that pulls c_i next (push);
+//   AA own:       read own site,                  write own site.
+template <class Store, bool kF64Mom, int SUB, int kEq, int kKind = kStepPingPong>
 __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
   using C = Codec<Store>;
   using R = typename C::Real;
@@ -508,23 +513,29 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
-    constexpr int dx = rd3q81::pull_disp(d.hx, SUB);
-    constexpr int dy = rd3q81::pull_disp(d.hy, SUB);
-    constexpr int dz = rd3q81::pull_disp(d.hz, SUB);
+    constexpr bool kPull = kKind != kStepAAOwn;
+    constexpr int dx = kPull ? rd3q81::pull_disp(d.hx, SUB) : 0;
+    constexpr int dy = kPull ? rd3q81::pull_disp(d.hy, SUB) : 0;
+    constexpr int dz = kPull ? rd3q81::pull_disp(d.hz, SUB) : 0;
     f[i] = C::load(static_cast<const Store*>(p.src_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
   });
   const auto mo = site_moments<Store, kF64Mom>(f, p.tab);
   site_relax<Store, typename decltype(mo)::value_type, kEq>(f, mo, p.omega, p.flag, p.tab);
-  const int own = zs[4] + ys[4] + xs[4];
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
-    C::store(static_cast<Store*>(p.dst_slab[SUB][i]) + own, f[i]);
+    constexpr rd3q81::Dir d = rd3q81::kDirs[i];
+    constexpr bool kPush = kKind == kStepAANeighbour;
+    constexpr int dx = kPush ? rd3q81::pull_disp(-d.hx, SUB) : 0;
+    constexpr int dy = kPush ? rd3q81::pull_disp(-d.hy, SUB) : 0;
+    constexpr int dz = kPush ? rd3q81::pull_disp(-d.hz, SUB) : 0;
+    C::store(static_cast<Store*>(p.dst_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]), f[i]);
   });
 }
 
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
 // 4 for FP32/FP16/BF16 storage with FP32 moments (<= 128 registers, 16 warps per SM), 3 for
-// FP32 with FP64 moments, and no bound for FP64 storage (its 81 doubles need ~250).
+// FP32 with FP64 moments and for the entropic alpha, and no bound for FP64 storage (its 81
+// doubles need ~250).
 template <class Store, bool kF64Mom, int kEq>
 constexpr int sc_min_blocks() {
   if constexpr (std::is_same_v<Store, double>) return 1;
@@ -532,19 +543,19 @@ constexpr int sc_min_blocks() {
   else return 4;
 }
 
-template <class Store, bool kF64Mom, int kEq>
+template <class Store, bool kF64Mom, int kEq, int kKind = kStepPingPong>
 __global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom, kEq>())
     stream_collide_kernel(const StepParams p) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const long long t = static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
   if (t >= n) return;
   if (blockIdx.y == 0)
-    site_update_slabs<Store, kF64Mom, 0, kEq>(p, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 0, kEq, kKind>(p, static_cast<int>(t));
   else
-    site_update_slabs<Store, kF64Mom, 1, kEq>(p, static_cast<int>(t));
+    site_update_slabs<Store, kF64Mom, 1, kEq, kKind>(p, static_cast<int>(t));
 }
 
-template <class Store, bool kF64Mom, int kEq = kEqSeries>
+template <class Store, bool kF64Mom, int kEq = kEqSeries, int kKind = kStepPingPong>
 cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
   const dim3 grid(static_cast<unsigned>((n + kScBlock - 1) / kScBlock), 2);
@@ -554,11 +565,30 @@ cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cs);
     if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
-      e = cudaFuncSetAttribute(stream_collide_kernel<Store, kF64Mom, kEq>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+      e = cudaFuncSetAttribute(stream_collide_kernel<Store, kF64Mom, kEq, kKind>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     if (e != cudaSuccess) return e;
   }
-  stream_collide_kernel<Store, kF64Mom, kEq><<<grid, kScBlock, 0, s>>>(p);
+  stream_collide_kernel<Store, kF64Mom, kEq, kKind><<<grid, kScBlock, 0, s>>>(p);
   return cudaGetLastError();
+}
+
+// Both AA kinds of one storage and equilibrium (the sc_aa_*.cu units).
+template <class Store, int kEq>
+cudaError_t launch_sc_aa(int kind, const StepParams& p, cudaStream_t s) {
+  return kind == kStepAAOwn ? launch_sc<Store, false, kEq, kStepAAOwn>(p, s)
+                            : launch_sc<Store, false, kEq, kStepAANeighbour>(p, s);
+}
+
+template <class Store>
+cudaError_t launch_sc_aa_all(int eq, int kind, const StepParams& p, cudaStream_t s) {
+  switch (eq) {
+    case kEqSeries: return launch_sc_aa<Store, kEqSeries>(kind, p, s);
+    case kEqSeriesExactW: return launch_sc_aa<Store, kEqSeriesExactW>(kind, p, s);
+    case kEqEntropic: return launch_sc_aa<Store, kEqEntropic>(kind, p, s);
+    case kEqEntropicAlpha: return launch_sc_aa<Store, kEqEntropicAlpha>(kind, p, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace lbm
