@@ -51,6 +51,8 @@ def parse():
                    help="for --quick runs: BGK (alpha = 2) or the entropic alpha (needs --equilibrium entropic)")
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-only", type=int, default=0, metavar="K",
+                   help="time only the end-to-end path (K steps at --n, --storage) and print it (for profiling)")
     p.add_argument("--served-only", type=int, default=0, metavar="N",
                    help="run only the served mixed batch with N requests (no FP64 comparison)")
     return p.parse_args()
@@ -399,6 +401,9 @@ def ours(args):
     rank, world, local = dist_setup(args)
     torch.cuda.set_device(local)
     from paper_2409_05114_gb300 import binding as B
+    if args.e2e_only:
+        print(json.dumps({"e2e": run_e2e(B, args.n, args.storage, args.e2e_only)}), flush=True)
+        return
     if args.served_only:
         print(json.dumps({"served": run_served(B, args.served_only, compare_fp64=False)}), flush=True)
         return
