@@ -27,10 +27,12 @@
  * AA streaming).  The caller owns every field buffer it passes; the library copies in or out
  * and keeps no caller pointer after a call returns.  on_device = 1 means the pointers are
  * device pointers of the context's device (for example a torch tensor's data_ptr()), read or
- * written in order on the context's stream; on_device = 0 means host memory.  For lbm_init
- * and lbm_moments, host fields that are page-locked and mapped (cudaHostAlloc /
- * cudaHostRegister, e.g. pinned torch tensors; each field one allocation) are read or written
- * in place by the kernel over the host link; pageable host memory goes through chunked copies.
+ * written in order on the context's stream; on_device = 0 means host memory.  Host fields
+ * that are page-locked (cudaHostAlloc / cudaHostRegister, e.g. pinned torch tensors; each
+ * field one allocation) move without extra host copies: lbm_init reads them in place from its
+ * kernel over the host link; lbm_moments and lbm_advance_fields move them with the copy
+ * engines, one z slab at a time through a ring of device staging slots (part of the context's
+ * footprint), overlapped with the kernels.  Pageable host memory goes through chunked copies.
  *
  * Errors.  Every call returns an lbm_status; no C++ exception crosses this interface.
  * A NULL or destroyed context gives LBM_EINVAL.  lbm_last_error() describes the last
@@ -149,6 +151,18 @@ lbm_status lbm_init(lbm_ctx* ctx, const double* rho, const double* u, const doub
  * pull-stream-collide kernel over all sites.  Stream-ordered: returns once the work is
  * queued.  Returns LBM_EINVAL if lbm_init / lbm_set_populations was never called. */
 lbm_status lbm_step(lbm_ctx* ctx, long long n);
+
+/* lbm_init, lbm_step(n) and lbm_moments as one call: sets every site to f~eq of the fields
+ * rho, u, theta, advances n >= 0 steps and writes the fields of the result to rho_out, u_out,
+ * theta_out (layouts as lbm_init; the outputs may be the inputs).  The context keeps the state
+ * afterwards, as after the three calls.  With page-locked host fields and ping-pong streaming
+ * the work runs slab by slab in z: the host-to-device copy of later slabs, the kernels, and the
+ * device-to-host copy of finished slabs overlap (both directions of the host link at once when
+ * n <= 1; for n >= 2 the input overlaps initialisation and the output overlaps the last step).
+ * Otherwise (device fields, pageable memory, AA streaming) the three calls run one after the
+ * other.  Synchronises; LBM_EUNSTABLE as lbm_moments; LBM_EINVAL for NULL fields or n < 0. */
+lbm_status lbm_advance_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, long long n,
+                              double* rho_out, double* u_out, double* theta_out, int on_device);
 
 /* rho, u, theta of the stored (post-collision) state, computed in FP64 (Eq. (conslaws));
  * layout as for lbm_init.  Synchronises the stream; returns LBM_EUNSTABLE (after writing

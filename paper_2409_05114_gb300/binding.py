@@ -75,6 +75,7 @@ def _load():
         "lbm_init": ([P, P, P, P, I], I),
         "lbm_step": ([P, LL], I),
         "lbm_moments": ([P, P, P, P, I], I),
+        "lbm_advance_fields": ([P, P, P, P, LL, P, P, P, I], I),
         "lbm_totals": ([P, P], I),
         "lbm_diagnostics": ([P, P], I),
         "lbm_selftest_log1p": ([LL, ctypes.POINTER(D)], I),
@@ -194,6 +195,14 @@ def lbm_moments(ctx, rho, u, theta):
     if not d0 == d1 == d2:
         raise ValueError("rho, u, theta must all be host arrays or all device tensors")
     _check(_lib.lbm_moments(ctx, pr, pu, pt, d0), ctx)
+
+
+def lbm_advance_fields(ctx, rho, u, theta, n: int, rho_out, u_out, theta_out):
+    ptrs = [_ptr(rho), _ptr(u), _ptr(theta), _ptr(rho_out, True), _ptr(u_out, True), _ptr(theta_out, True)]
+    if len({d for _, d in ptrs}) != 1:
+        raise ValueError("all six fields must be host arrays or all device tensors")
+    (pr, d0), (pu, _), (pt, _), (qr, _), (qu, _), (qt, _) = ptrs
+    _check(_lib.lbm_advance_fields(ctx, pr, pu, pt, int(n), qr, qu, qt, d0), ctx)
 
 
 def lbm_totals(ctx) -> np.ndarray:

@@ -1,9 +1,11 @@
 // C-ABI of liblbm_rd3q81 (declared and documented in include/lbm.h): context lifetime,
 // validation, device memory, chunked host transfers and the step loop.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "lbm.h"
 #include "device_common.cuh"
@@ -13,6 +15,13 @@ namespace {
 constexpr uint32_t kMagic = 0x52443831u;  // "RD81"
 constexpr long long kChunkSites = 1LL << 22;  // sites per host-transfer chunk
 constexpr int kGraphSteps = 8;                // steps per replayed CUDA graph (even)
+// Pinned host fields move through staging slots, one z slab of both sublattices at a time:
+// a slab holds about kSlabSites sites per sublattice (whole planes), and kRing slots per
+// direction let the copy engines run ahead of (host to device) or behind (device to host)
+// the kernels.
+constexpr long long kSlabSites = 1LL << 20;
+constexpr int kRing = 3;
+constexpr int kSlabRows = 10;  // rho (2 sublattices), u (3 components x 2), theta (2)
 
 thread_local std::string g_create_error = "no error";
 
@@ -124,6 +133,13 @@ struct lbm_ctx {
   lbm::Feq81 feq_in[2]{};
   lbm::Feq81 feq_in_own[2]{};  // feq_in with direction i in the slot of -c_i (AA own layout)
   long long launches = 0;
+  // Staged host transfers: copy streams, slot events, kRing input then kRing output slots.
+  cudaStream_t xfer_in = nullptr, xfer_out = nullptr;
+  cudaEvent_t in_ready[kRing] = {}, in_free[kRing] = {}, out_ready[kRing] = {}, out_free[kRing] = {};
+  cudaEvent_t mark = nullptr;
+  double* d_stage = nullptr;
+  int slab_planes = 0;
+  long long slab_m = 0;  // sites per sublattice in a full slab (the row pitch of a slot)
   cudaGraphExec_t graph = nullptr;  // kGraphSteps steps starting from buffer 0 (AA: the own layout)
   long long graph_launches = 0;     // kernel launches in one replay
   long long direct_steps = 0;       // steps issued by plain launches (the first ones load the kernels)
@@ -159,6 +175,17 @@ long long scratch_doubles(long long sites) {
   return a > b ? a : b;
 }
 size_t scratch_bytes(long long sites) { return static_cast<size_t>(scratch_doubles(sites)) * sizeof(double); }
+
+// z planes per staged slab, and the staging bytes (2 kRing slots of kSlabRows rows).
+int slab_planes(int nx, int ny, int nz) {
+  const long long nxy = static_cast<long long>(nx) * ny;
+  const long long z = kSlabSites / nxy;
+  return static_cast<int>(z < 1 ? 1 : z > nz ? nz : z);
+}
+size_t stage_bytes(int nx, int ny, int nz) {
+  const long long m = static_cast<long long>(slab_planes(nx, ny, nz)) * nx * ny;
+  return static_cast<size_t>(2 * kRing * kSlabRows * m) * sizeof(double);
+}
 
 size_t aux_bytes(const lbm::Geometry& g) {
   return static_cast<size_t>(lbm::totals_blocks(g)) * 5 * sizeof(double) + 8 * sizeof(double) + 256;
@@ -209,7 +236,7 @@ lbm_status lbm_footprint(const lbm_config* cfg, size_t* bytes) {
   if (lbm::plan_geometry(cfg, &g, &why) != LBM_OK) return fail(nullptr, LBM_EINVAL, why);
   const long long sites = 2LL * cfg->nx * cfg->ny * cfg->nz;
   *bytes = (cfg->streaming == LBM_STREAM_AA ? 1 : 2) * buffer_bytes(g, cfg->storage) + scratch_bytes(sites) +
-           aux_bytes(g);
+           aux_bytes(g) + stage_bytes(cfg->nx, cfg->ny, cfg->nz);
   return LBM_OK;
 }
 
@@ -275,10 +302,23 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_totals, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_flag, 256);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flag, 0, 256, ctx->stream);
+  ctx->slab_planes = slab_planes(cfg->nx, cfg->ny, cfg->nz);
+  ctx->slab_m = static_cast<long long>(ctx->slab_planes) * cfg->nx * cfg->ny;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_stage, stage_bytes(cfg->nx, cfg->ny, cfg->nz));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return bail(LBM_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
+  e = cudaStreamCreateWithFlags(&ctx->xfer_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_out, cudaStreamNonBlocking);
+  for (int k = 0; k < kRing && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&ctx->in_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->in_free[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->out_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->out_free[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->mark, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(LBM_ECUDA, std::string("stream/event creation failed: ") + cudaGetErrorString(e));
   *out = ctx;
   return LBM_OK;
 }
@@ -345,6 +385,7 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long l
   p.flag = ctx->d_flag;
   p.tab = ctx->tab;
   cudaError_t e = cudaSuccess;
+  static_assert(kGraphSteps % 2 == 0, "a captured run must return to its starting state");
   if (!ctx->aa) {
     for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
       if (!ctx->zero_grad[face]) continue;
@@ -419,13 +460,8 @@ cudaError_t build_graph(lbm_ctx* ctx) {
   return e;
 }
 
-}  // namespace
-
-lbm_status lbm_step(lbm_ctx* ctx, long long n) {
-  if (!valid(ctx)) return LBM_EINVAL;
-  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
-  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
-  DeviceGuard dg(ctx->device);
+// n steps on the context's stream (lbm_step after its checks).
+lbm_status run_steps(lbm_ctx* ctx, long long n) {
   // Runs of kGraphSteps steps are replayed from one captured graph (launch overhead matters
   // for small grids), unless the caller is capturing the context's stream itself.
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -455,6 +491,228 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n) {
   return LBM_OK;
 }
 
+
+// ---- staged host transfers --------------------------------------------------------------
+// A slab is the z planes [z0, z1) of both sublattices.  In a staging slot its fields are
+// kSlabRows rows of slab_m doubles: rows 0-1 rho, 2-7 u (row 2a + s: component a on
+// sublattice s), 8-9 theta.  In the field layout the same rows start s n, (2a + s) n and s n
+// elements into the field (n = nx ny nz), plus z0 nx ny: one 2-D copy per field.
+struct Slab {
+  int z0, z1;
+  long long m;  // sites per sublattice
+};
+
+int slab_count(const lbm_ctx* ctx) { return (ctx->cfg.nz + ctx->slab_planes - 1) / ctx->slab_planes; }
+
+Slab slab_at(const lbm_ctx* ctx, int k) {
+  const int z0 = k * ctx->slab_planes;
+  const int z1 = z0 + ctx->slab_planes < ctx->cfg.nz ? z0 + ctx->slab_planes : ctx->cfg.nz;
+  return {z0, z1, static_cast<long long>(z1 - z0) * ctx->cfg.nx * ctx->cfg.ny};
+}
+
+// Slot q % kRing of the input (out = 0) or output (out = 1) ring.
+double* stage_slot(const lbm_ctx* ctx, int out, long long q) {
+  return ctx->d_stage + ((out ? kRing : 0) + q % kRing) * kSlabRows * ctx->slab_m;
+}
+
+cudaError_t copy_slab(const lbm_ctx* ctx, const Slab& sl, double* slot, double* const host[3], bool to_device,
+                      cudaStream_t s) {
+  const long long nxy = static_cast<long long>(ctx->cfg.nx) * ctx->cfg.ny;
+  const size_t width = static_cast<size_t>(sl.m) * sizeof(double);
+  const size_t hp = static_cast<size_t>(nxy * ctx->cfg.nz) * sizeof(double);
+  const size_t dp = static_cast<size_t>(ctx->slab_m) * sizeof(double);
+  const int row0[3] = {0, 2, 8}, rows[3] = {2, 6, 2};
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < 3 && e == cudaSuccess; ++f) {
+    double* d = slot + row0[f] * ctx->slab_m;
+    double* h = host[f] + sl.z0 * nxy;
+    e = to_device ? cudaMemcpy2DAsync(d, dp, h, hp, width, rows[f], cudaMemcpyHostToDevice, s)
+                  : cudaMemcpy2DAsync(h, hp, d, dp, width, rows[f], cudaMemcpyDeviceToHost, s);
+  }
+  return e;
+}
+
+// Host to device copy of slab k's fields into input slot k, once lbm::launch_init is done with
+// the slot's previous slab.
+cudaError_t stage_in(lbm_ctx* ctx, int k, double* const host[3]) {
+  const int r = k % kRing;
+  cudaError_t e = cudaStreamWaitEvent(ctx->xfer_in, ctx->in_free[r], 0);
+  if (e == cudaSuccess) e = copy_slab(ctx, slab_at(ctx, k), stage_slot(ctx, 0, k), host, true, ctx->xfer_in);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->in_ready[r], ctx->xfer_in);
+  return e;
+}
+
+// Equilibrium initialisation of slab k from its input slot (buffer 0), and the zero-gradient
+// ghosts of its planes when a step follows.
+cudaError_t init_slab(lbm_ctx* ctx, int k, bool fill_ghosts) {
+  const int r = k % kRing;
+  const Slab sl = slab_at(ctx, k);
+  const long long n = ctx->sites / 2, M = ctx->slab_m, nxy = static_cast<long long>(ctx->cfg.nx) * ctx->cfg.ny;
+  double* slot = stage_slot(ctx, 0, k);
+  cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->in_ready[r], 0);
+  for (int sub = 0; sub < 2 && e == cudaSuccess; ++sub) {
+    e = lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], slot + sub * M,
+                         slot + (2 + sub) * M, slot + (8 + sub) * M, sub * n + sl.z0 * nxy, sl.m, 2 * M, ctx->stream,
+                         ctx->d_flag, 0);
+    ++ctx->launches;
+  }
+  for (int face = 0; face < 2 && e == cudaSuccess && fill_ghosts; ++face) {
+    if (!ctx->zero_grad[face]) continue;
+    e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, ctx->stream, sl.z0, sl.z1);
+    ++ctx->launches;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->in_free[r], ctx->stream);
+  return e;
+}
+
+// Moments of slab k of `buf` into output slot q (once that slot's previous copy has left),
+// then its device to host copy on the output copy stream.
+cudaError_t moments_out(lbm_ctx* ctx, int k, long long q, const void* buf, int layout, double* const host[3]) {
+  const int r = q % kRing;
+  const Slab sl = slab_at(ctx, k);
+  const long long n = ctx->sites / 2, M = ctx->slab_m, nxy = static_cast<long long>(ctx->cfg.nx) * ctx->cfg.ny;
+  double* slot = stage_slot(ctx, 1, q);
+  cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->out_free[r], 0);
+  for (int sub = 0; sub < 2 && e == cudaSuccess; ++sub) {
+    e = lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, buf, slot + sub * M, slot + (2 + sub) * M,
+                            slot + (8 + sub) * M, sub * n + sl.z0 * nxy, sl.m, 2 * M, ctx->stream, layout);
+    ++ctx->launches;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->out_ready[r], ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer_out, ctx->out_ready[r], 0);
+  if (e == cudaSuccess) e = copy_slab(ctx, sl, slot, host, false, ctx->xfer_out);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->out_free[r], ctx->xfer_out);
+  return e;
+}
+
+// One ping-pong step over the planes of slab k (buffer cur into cur ^ 1; ghosts already filled).
+cudaError_t slab_step(lbm_ctx* ctx, int k) {
+  const Slab sl = slab_at(ctx, k);
+  lbm::StepParams p;
+  p.g = ctx->g;
+  p.omega = ctx->omega;
+  p.flag = ctx->d_flag;
+  p.tab = ctx->tab;
+  p.src = ctx->buf[ctx->cur];
+  p.dst = ctx->buf[ctx->cur ^ 1];
+  lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepPingPong);
+  p.z0 = sl.z0;
+  p.z1 = sl.z1;
+  ++ctx->launches;
+  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, step_mode(ctx), lbm::kStepPingPong, p,
+                                    ctx->stream);
+}
+
+// The copy streams start after the work already queued on the context's stream ...
+cudaError_t fork_copies(lbm_ctx* ctx) {
+  cudaError_t e = cudaEventRecord(ctx->mark, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer_in, ctx->mark, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer_out, ctx->mark, 0);
+  return e;
+}
+
+// ... and the context's stream continues after their last copy.
+cudaError_t join_copies(lbm_ctx* ctx) {
+  cudaError_t e = cudaSuccess;
+  for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out}) {
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->mark, xs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->mark, 0);
+  }
+  return e;
+}
+
+// lbm_advance_fields for pinned host fields and ping-pong streaming.  Slab by slab: the input
+// copy engine fills input slots, init runs on each slab as it lands, and the output copy
+// engine drains each slab's moments as soon as they are computed, so both directions of the
+// host link and the kernels overlap.  n == 0: moments follow init; n == 1: the step of a slab
+// follows the init of every slab within the pull reach of its planes; n >= 2: init for all
+// slabs, n - 1 whole-grid steps, then the last step slab by slab with its moments.
+lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double* const out[3]) {
+  const int N = slab_count(ctx);
+  ctx->cur = 0;
+  ctx->layout = lbm::kLayoutPlain;
+  ctx->initialized = false;
+  LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
+  lbm_status st = fill_inflow_faces(ctx);
+  if (st != LBM_OK) return st;
+  LBM_CK(ctx, fork_copies(ctx));
+  for (int k = 0; k < N && k < kRing; ++k) LBM_CK(ctx, stage_in(ctx, k, in));
+  // n == 1: need[k] = the last slab, in init order, holding a plane within kReach of slab k
+  std::vector<int> need(N, 0), order(N);
+  for (int k = 0; k < N; ++k) {
+    order[k] = k;
+    const Slab sl = slab_at(ctx, k);
+    for (int z = sl.z0 - rd3q81::kReach; z < sl.z1 + rd3q81::kReach; ++z) {
+      const int zz = ((z % ctx->cfg.nz) + ctx->cfg.nz) % ctx->cfg.nz;
+      need[k] = std::max(need[k], zz / ctx->slab_planes);
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return need[a] < need[b]; });
+  size_t next = 0;
+  long long q = 0;
+  for (int j = 0; j < N; ++j) {
+    LBM_CK(ctx, init_slab(ctx, j, n == 1));
+    if (j + kRing < N) LBM_CK(ctx, stage_in(ctx, j + kRing, in));
+    if (n == 0) {
+      LBM_CK(ctx, moments_out(ctx, j, q++, ctx->buf[0], lbm::kLayoutPlain, out));
+    } else if (n == 1) {
+      for (; next < order.size() && need[order[next]] <= j; ++next) {
+        LBM_CK(ctx, slab_step(ctx, order[next]));
+        LBM_CK(ctx, moments_out(ctx, order[next], q++, ctx->buf[1], lbm::kLayoutPlain, out));
+      }
+    }
+  }
+  ctx->initialized = true;
+  if (n >= 2) {
+    st = run_steps(ctx, n - 1);
+    if (st != LBM_OK) return st;
+    for (int face = 0; face < 2; ++face) {
+      if (!ctx->zero_grad[face]) continue;
+      LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
+      ++ctx->launches;
+    }
+    for (int k = 0; k < N; ++k) {
+      LBM_CK(ctx, slab_step(ctx, k));
+      LBM_CK(ctx, moments_out(ctx, k, q++, ctx->buf[ctx->cur ^ 1], lbm::kLayoutPlain, out));
+    }
+  }
+  if (n >= 1) advance(ctx);
+  LBM_CK(ctx, join_copies(ctx));
+  return check_flag(ctx);
+}
+
+}  // namespace
+
+lbm_status lbm_step(lbm_ctx* ctx, long long n) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
+  if (!ctx->initialized) return fail(ctx, LBM_EINVAL, "lbm_init or lbm_set_populations was never called");
+  DeviceGuard dg(ctx->device);
+  return run_steps(ctx, n);
+}
+
+lbm_status lbm_advance_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, long long n,
+                              double* rho_out, double* u_out, double* theta_out, int on_device) {
+  if (!valid(ctx)) return LBM_EINVAL;
+  if (!rho || !u || !theta || !rho_out || !u_out || !theta_out) return fail(ctx, LBM_EINVAL, "NULL field pointer");
+  if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
+  DeviceGuard dg(ctx->device);
+  bool pinned = !on_device && !ctx->aa;
+  for (const void* f : {static_cast<const void*>(rho), static_cast<const void*>(u), static_cast<const void*>(theta),
+                        static_cast<const void*>(rho_out), static_cast<const void*>(u_out),
+                        static_cast<const void*>(theta_out)})
+    if (pinned && !mapped_host(f)) pinned = false;
+  if (pinned) {
+    double* const in[3] = {const_cast<double*>(rho), const_cast<double*>(u), const_cast<double*>(theta)};
+    double* const out[3] = {rho_out, u_out, theta_out};
+    return advance_staged(ctx, in, n, out);
+  }
+  lbm_status st = lbm_init(ctx, rho, u, theta, on_device);
+  if (st == LBM_OK) st = run_steps(ctx, n);
+  if (st == LBM_OK) st = lbm_moments(ctx, rho_out, u_out, theta_out, on_device);
+  return st;
+}
+
 lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int on_device) {
   if (!valid(ctx)) return LBM_EINVAL;
   if (!rho || !u || !theta) return fail(ctx, LBM_EINVAL, "NULL field pointer");
@@ -462,15 +720,17 @@ lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int 
   DeviceGuard dg(ctx->device);
   const long long S = ctx->sites;
   const void* b = ctx->buf[ctx->cur];
-  void* hr = on_device ? nullptr : mapped_host(rho);
-  void* hu = on_device ? nullptr : mapped_host(u);
-  void* ht = on_device ? nullptr : mapped_host(theta);
-  if (on_device || (hr && hu && ht)) {
-    // device fields, or pinned host fields written in place by the kernel
-    LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, on_device ? rho : static_cast<double*>(hr),
-                                    on_device ? u : static_cast<double*>(hu),
-                                    on_device ? theta : static_cast<double*>(ht), 0, S, S, ctx->stream, ctx->layout));
+  const bool pinned = !on_device && mapped_host(rho) && mapped_host(u) && mapped_host(theta);
+  if (on_device) {
+    LBM_CK(ctx, lbm::launch_moments(ctx->storage, ctx->g, ctx->tab, b, rho, u, theta, 0, S, S, ctx->stream,
+                                    ctx->layout));
     ++ctx->launches;
+  } else if (pinned) {
+    // slab by slab through the output ring: the copy engine drains one slab while the next
+    // one's moments are computed
+    double* const out[3] = {rho, u, theta};
+    for (int k = 0; k < slab_count(ctx); ++k) LBM_CK(ctx, moments_out(ctx, k, k, b, ctx->layout, out));
+    LBM_CK(ctx, join_copies(ctx));
   } else {
     double* sr = ctx->d_scratch;
     double* su = sr + ctx->chunk;
@@ -630,7 +890,8 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (!valid(ctx)) return LBM_EINVAL;
   {
     DeviceGuard dg(ctx->device);
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t xs : {ctx->stream, ctx->xfer_in, ctx->xfer_out})
+      if (xs) cudaStreamSynchronize(xs);
     for (int b = 0; b < 2; ++b)
       if (ctx->buf[b]) cudaFree(ctx->buf[b]);
     if (ctx->d_scratch) cudaFree(ctx->d_scratch);
@@ -638,6 +899,13 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
     if (ctx->d_totals) cudaFree(ctx->d_totals);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out})
+      if (xs) cudaStreamDestroy(xs);
+    for (int k = 0; k < kRing; ++k)
+      for (cudaEvent_t ev : {ctx->in_ready[k], ctx->in_free[k], ctx->out_ready[k], ctx->out_free[k]})
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->mark) cudaEventDestroy(ctx->mark);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   }
   ctx->magic = 0;

@@ -103,14 +103,25 @@ __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTab
                                              double& jz, double& e) {
   const long long off = site_offset(g, sub, t);
   using R = typename Codec<S>::Real;
+  R fv[kQ];
+  if (layout == kLayoutPlain) {
+    static_for<kQ>([&](auto Ic) {
+      constexpr int i = decltype(Ic)::value;
+      fv[i] = Codec<S>::load(buf + off + i * g.dir_stride);
+    });
+  } else {
+    static_for<kQ>([&](auto Ic) {
+      constexpr int i = decltype(Ic)::value;
+      fv[i] = Codec<S>::load(buf + pop_offset(g, tab, layout, sub, t, i));
+    });
+  }
   R sr[kShells], sx[kShells], sy[kShells], sz[kShells];
 #pragma unroll
   for (int s = 0; s < kShells; ++s) sr[s] = sx[s] = sy[s] = sz[s] = R(0);
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
-    const R f = Codec<S>::load(buf + (layout == kLayoutPlain ? off + i * g.dir_stride
-                                                             : pop_offset(g, tab, layout, sub, t, i)));
+    const R f = fv[i];
     sr[d.shell] += f;
     if constexpr (d.hx != 0) sx[d.shell] += R(0.5 * d.hx) * f;
     if constexpr (d.hy != 0) sy[d.shell] += R(0.5 * d.hy) * f;
@@ -133,6 +144,136 @@ __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTab
   }
 }
 
+// ---- double-word arithmetic: a value hi + lo of two floats, |lo| <= ulp(hi) / 2 -----------------
+// About 48 significant bits from FP32 operations, which this part runs some 60 times faster than
+// FP64.  The building blocks are the error-free transformations TwoSum (Knuth), Fast2Sum
+// (Dekker) and TwoProd through a fused multiply-add; sums, products and the reciprocal combine
+// them as in the double-word algorithms analysed by Joldes, Muller and Popescu (ACM TOMS 44,
+// 2017), each with a relative error of a few units of 2^-48.  The __f*_rn intrinsics keep the
+// compiler from contracting or reassociating any step.
+struct Dw {
+  float hi, lo;
+};
+
+__device__ __forceinline__ Dw two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv))};
+}
+
+__device__ __forceinline__ Dw fast_two_sum(float a, float b) {  // needs |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ Dw two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ Dw dw_add(Dw x, float y) {
+  const Dw s = two_sum(x.hi, y);
+  return fast_two_sum(s.hi, __fadd_rn(x.lo, s.lo));
+}
+
+__device__ __forceinline__ Dw dw_add(Dw x, Dw y) {
+  const Dw s = two_sum(x.hi, y.hi), t = two_sum(x.lo, y.lo);
+  const Dw v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+
+__device__ __forceinline__ Dw dw_mul(Dw x, Dw y) {
+  const Dw c = two_prod(x.hi, y.hi);
+  const float cross = __fmaf_rn(x.lo, y.hi, __fmul_rn(x.hi, y.lo));
+  return fast_two_sum(c.hi, __fadd_rn(c.lo, cross));
+}
+
+// 1 / y: the rounded FP32 reciprocal t, then one Newton step t + t (1 - y t) with the residual
+// formed exactly enough (1 - y.hi t by TwoProd, exact by Sterbenz' lemma).
+__device__ __forceinline__ Dw dw_recip(Dw y) {
+  const float t = __frcp_rn(y.hi);
+  const Dw p = two_prod(y.hi, t);
+  const float d = __fsub_rn(__fsub_rn(1.0f, p.hi), __fmaf_rn(y.lo, t, p.lo));
+  return fast_two_sum(t, __fmul_rn(d, t));
+}
+
+__device__ __forceinline__ double dw_to_double(Dw x) {
+  return static_cast<double>(x.hi) + static_cast<double>(x.lo);
+}
+
+// Moments of one site of FP32 / FP16 / BF16 storage as double words.  The shell sums are FP32 as
+// in site_moments; FP32 populations are then combined shell by shell in double words.  Offset
+// storage combines the weighted offset sums (deviations from the weights' moments, small) in
+// FP32 and adds the reference 1 and 3 theta0 in double words.
+template <class S>
+__device__ __forceinline__ void site_moments_dw(const Geometry& g, const LatticeTables& tab, const S* buf,
+                                                int layout, int sub, long long t, Dw& rho, Dw& jx, Dw& jy, Dw& jz,
+                                                Dw& e) {
+  const long long off = site_offset(g, sub, t);
+  // all 81 loads first, in one branch-free run per layout: the site waits on one round trip
+  // to memory, not 81
+  float fv[kQ];
+  if (layout == kLayoutPlain) {
+    static_for<kQ>([&](auto Ic) {
+      constexpr int i = decltype(Ic)::value;
+      fv[i] = Codec<S>::load(buf + off + i * g.dir_stride);
+    });
+  } else {
+    static_for<kQ>([&](auto Ic) {
+      constexpr int i = decltype(Ic)::value;
+      fv[i] = Codec<S>::load(buf + pop_offset(g, tab, layout, sub, t, i));
+    });
+  }
+  float sr[kShells], sx[kShells], sy[kShells], sz[kShells];
+#pragma unroll
+  for (int s = 0; s < kShells; ++s) sr[s] = sx[s] = sy[s] = sz[s] = 0.0f;
+  static_for<kQ>([&](auto Ic) {
+    constexpr int i = decltype(Ic)::value;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[i];
+    const float f = fv[i];
+    sr[d.shell] += f;
+    if constexpr (d.hx != 0) sx[d.shell] += 0.5f * d.hx * f;
+    if constexpr (d.hy != 0) sy[d.shell] += 0.5f * d.hy * f;
+    if constexpr (d.hz != 0) sz[d.shell] += 0.5f * d.hz * f;
+  });
+  if constexpr (Codec<S>::kOffset) {
+    float dr = 0.0f, dx = 0.0f, dy = 0.0f, dz = 0.0f, de = 0.0f;
+    static_for<kShells>([&](auto Sc) {
+      constexpr int s = decltype(Sc)::value;
+      constexpr float c2 = static_cast<float>(rd3q81::kShellC2[s]);
+      const float w = tab.wf[s];
+      dr = fmaf(w, sr[s], dr);
+      dx = fmaf(w, sx[s], dx);
+      dy = fmaf(w, sy[s], dy);
+      dz = fmaf(w, sz[s], dz);
+      de = fmaf(w * c2, sr[s], de);
+    });
+    rho = two_sum(1.0f, dr);
+    jx = {dx, 0.0f};
+    jy = {dy, 0.0f};
+    jz = {dz, 0.0f};
+    e = dw_add(Dw{tab.theta0x3_dw[0], tab.theta0x3_dw[1]}, de);
+  } else {
+    rho = jx = jy = jz = e = Dw{0.0f, 0.0f};
+    static_for<kShells>([&](auto Sc) {
+      constexpr int s = decltype(Sc)::value;
+      constexpr float c2 = static_cast<float>(rd3q81::kShellC2[s]);  // multiples of 1/4: exact
+      rho = dw_add(rho, sr[s]);
+      jx = dw_add(jx, sx[s]);
+      jy = dw_add(jy, sy[s]);
+      jz = dw_add(jz, sz[s]);
+      if constexpr (c2 != 0.0f) {
+        const Dw p = two_prod(c2, sr[s]);
+        e = dw_add(dw_add(e, p.hi), p.lo);
+      }
+    });
+  }
+}
+
+// rho, u = j / rho and theta = (e / rho - u.u) / 3 per site (Eq. (conslaws)), returned in FP64.
+// FP64 storage sums and divides in FP64.  The narrower storage types carry the shell sums'
+// FP32 rounding and otherwise double-word accuracy (relative ~1e-14 beyond the shell sums),
+// with 15 FP64 operations a site (the final conversions), not the ~250 of an FP64 combination.
 template <class S>
 __global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, int layout, double* rho, double* u,
                                double* theta, long long first, long long count, long long us) {
@@ -141,14 +282,30 @@ __global__ void moments_kernel(Geometry g, LatticeTables tab, const S* buf, int 
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
   const long long gs = first + k;
   const int sub = gs >= n ? 1 : 0;
-  double r, jx, jy, jz, e;
-  site_moments<S>(g, tab, buf, layout, sub, gs - sub * n, r, jx, jy, jz, e);
-  const double ux = jx / r, uy = jy / r, uz = jz / r;
-  rho[k] = r;
-  u[k] = ux;
-  u[us + k] = uy;
-  u[2 * us + k] = uz;
-  theta[k] = (e / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+  if constexpr (std::is_same_v<S, double>) {
+    double r, jx, jy, jz, e;
+    site_moments<S>(g, tab, buf, layout, sub, gs - sub * n, r, jx, jy, jz, e);
+    const double ux = jx / r, uy = jy / r, uz = jz / r;
+    rho[k] = r;
+    u[k] = ux;
+    u[us + k] = uy;
+    u[2 * us + k] = uz;
+    theta[k] = (e / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+  } else {
+    constexpr float kThirdHi = static_cast<float>(1.0 / 3.0);
+    constexpr float kThirdLo = static_cast<float>(1.0 / 3.0 - static_cast<double>(kThirdHi));
+    Dw r, jx, jy, jz, e;
+    site_moments_dw<S>(g, tab, buf, layout, sub, gs - sub * n, r, jx, jy, jz, e);
+    const Dw inv = dw_recip(r);
+    const Dw ux = dw_mul(jx, inv), uy = dw_mul(jy, inv), uz = dw_mul(jz, inv);
+    const Dw u2 = dw_add(dw_add(dw_mul(ux, ux), dw_mul(uy, uy)), dw_mul(uz, uz));
+    const Dw th3 = dw_add(dw_mul(e, inv), Dw{-u2.hi, -u2.lo});
+    rho[k] = dw_to_double(r);
+    u[k] = dw_to_double(ux);
+    u[us + k] = dw_to_double(uy);
+    u[2 * us + k] = dw_to_double(uz);
+    theta[k] = dw_to_double(dw_mul(th3, Dw{kThirdHi, kThirdLo}));
+  }
 }
 
 // Dense FP64 layout f[sub][i][z][y][x] <-> padded storage.
@@ -197,14 +354,14 @@ __global__ void probe_kernel(Geometry g, LatticeTables tab, const S* buf, int la
 // Ghost layers of one x face: thread per (sub, i, z, y) row.  Zero gradient copies the
 // nearest interior site of the same sublattice into all kReach layers; inflow writes feq.
 template <class S>
-__global__ void zero_gradient_kernel(Geometry g, S* buf, int face) {
-  const long long rows = 2LL * kQ * g.nz * g.ny;
+__global__ void zero_gradient_kernel(Geometry g, S* buf, int face, int z0, int nzr) {
+  const long long rows = 2LL * kQ * nzr * g.ny;
   const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
   if (k >= rows) return;
   const int y = static_cast<int>(k % g.ny);
   const long long r = k / g.ny;
-  const int z = static_cast<int>(r % g.nz);
-  const long long si = r / g.nz;  // sub * kQ + i
+  const int z = z0 + static_cast<int>(r % nzr);
+  const long long si = r / nzr;  // sub * kQ + i
   const long long row = (si / kQ) * g.sub_stride + (si % kQ) * g.dir_stride + z * g.plane +
                         static_cast<long long>(y) * g.pitch;
   if (face == 0) {
@@ -372,10 +529,14 @@ cudaError_t launch_set_populations(int storage, const Geometry& g, const Lattice
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s) {
-  const long long rows = 2LL * kQ * g.nz * g.ny;
+cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s,
+                                      int z0, int z1) {
+  if (z1 < 0) z1 = g.nz;
+  if (z0 < 0 || z1 > g.nz) return cudaErrorInvalidValue;
+  if (z1 <= z0) return cudaSuccess;
+  const long long rows = 2LL * kQ * (z1 - z0) * g.ny;
   LBM_STORAGE_DISPATCH(storage, (zero_gradient_kernel<S><<<blocks_for(rows), kAuxBlock, 0, s>>>(
-                                    g, static_cast<S*>(buf), face)));
+                                    g, static_cast<S*>(buf), face, z0, z1 - z0)));
   return cudaGetLastError();
 }
 
@@ -421,6 +582,7 @@ cudaError_t launch_aa_ghost_push(int storage, const Geometry& g, const LatticeTa
 
 cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, int kind, const StepParams& p,
                                   cudaStream_t s) {
+  if (p.z0 < 0 || p.z1 > p.g.nz) return cudaErrorInvalidValue;
   if (kind != kStepPingPong) {
     if (fp64_moments) return cudaErrorInvalidValue;
     switch (storage) {

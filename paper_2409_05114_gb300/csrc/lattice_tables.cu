@@ -64,6 +64,8 @@ void build_lattice_tables(LatticeTables* t) {
     t->nbf[k] = static_cast<float>(t->nb[k]);
   }
   t->theta0f = static_cast<float>(t0);
+  t->theta0x3_dw[0] = static_cast<float>(3.0 * t0);
+  t->theta0x3_dw[1] = static_cast<float>(3.0 * t0 - static_cast<double>(t->theta0x3_dw[0]));
   for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
   for (int i = 0; i < kQ; ++i) {
     t->opp[i] = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
@@ -82,6 +84,8 @@ void fill_slab_bases(StepParams* p, size_t elem, int kind) {
   const char* src = static_cast<const char*>(p->src);
   char* dst = static_cast<char*>(p->dst);
   const long long e = static_cast<long long>(elem);
+  p->z0 = 0;
+  p->z1 = p->g.nz;
   for (int sub = 0; sub < 2; ++sub)
     for (int i = 0; i < kQ; ++i) {
       const int other = (rd3q81::kDirs[i].hx % 2 != 0) ? 1 - sub : sub;  // sublattice across link i

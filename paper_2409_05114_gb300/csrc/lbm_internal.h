@@ -40,6 +40,7 @@ struct LatticeTables {
   float pf[kShells][5];
   float naf[5], nbf[5];
   float theta0f;
+  float theta0x3_dw[2];  // 3 theta0 as a double word hi + lo (moment read-back of offset storage)
   double wdir[kQ];  // w_i per direction (decoding offset storage in the auxiliary kernels)
   // In-place (AA) streaming: opp[i] = index of -c_i; the site that pulls f_i from site n of
   // sublattice s is n - push_d[s][i][0..2] on sublattice push_d[s][i][3].
@@ -86,6 +87,9 @@ struct StepParams {
   // fill_slab_bases(); they spare the kernel the 64-bit slab arithmetic of every access.
   const void* src_slab[2][kQ];
   void* dst_slab[2][kQ];
+  // The update covers the z planes [z0, z1) of both sublattices (fill_slab_bases sets the
+  // whole grid, 0 and nz; a narrower range lets a step run slab by slab).
+  int z0, z1;
 };
 
 // Fills p.src_slab / p.dst_slab from p.src, p.dst, p.g and the element size, for a step of
@@ -163,7 +167,9 @@ struct Feq81 {
 };
 cudaError_t launch_fill_inflow(int storage, const Geometry& g, const LatticeTables& tab, void* buf,
                                int face, const Feq81& feq, cudaStream_t s);
-cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s);
+// Zero-gradient ghost layers of one x face, for the z planes [z0, z1) (z1 < 0: through nz).
+cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s,
+                                      int z0 = 0, int z1 = -1);
 // AA: after a neighbour step, what the ghost sites of one x face push into the interior.
 cudaError_t launch_aa_ghost_push(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
                                  int zero_grad, const Feq81& feq, cudaStream_t s);

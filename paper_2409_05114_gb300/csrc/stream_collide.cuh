@@ -546,9 +546,9 @@ constexpr int sc_min_blocks() {
 template <class Store, bool kF64Mom, int kEq, int kKind = kStepPingPong>
 __global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom, kEq>())
     stream_collide_kernel(const StepParams p) {
-  const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
-  const long long t = static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
-  if (t >= n) return;
+  const long long nxy = static_cast<long long>(p.g.nx) * p.g.ny;
+  const long long t = p.z0 * nxy + static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
+  if (t >= p.z1 * nxy) return;
   if (blockIdx.y == 0)
     site_update_slabs<Store, kF64Mom, 0, kEq, kKind>(p, static_cast<int>(t));
   else
@@ -557,7 +557,8 @@ __global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom, kEq>()
 
 template <class Store, bool kF64Mom, int kEq = kEqSeries, int kKind = kStepPingPong>
 cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
-  const long long n = static_cast<long long>(p.g.nx) * p.g.ny * p.g.nz;
+  const long long n = static_cast<long long>(p.g.nx) * p.g.ny * (p.z1 - p.z0);
+  if (n <= 0) return cudaSuccess;
   const dim3 grid(static_cast<unsigned>((n + kScBlock - 1) / kScBlock), 2);
   if constexpr (kEq == kEqEntropicAlpha) {
     // the alpha solve keeps 2 x 81 values per thread in local memory: all of L1 for it (set on

@@ -113,4 +113,5 @@ def test_null_context_calls_are_einval(B):
     assert lib.lbm_sync(None) == B.LBM_EINVAL
     assert lib.lbm_destroy(None) == B.LBM_EINVAL
     assert lib.lbm_totals(None, None) == B.LBM_EINVAL
+    assert lib.lbm_advance_fields(None, None, None, None, 1, None, None, None, 0) == B.LBM_EINVAL
     assert lib.lbm_last_error(None) is not None
