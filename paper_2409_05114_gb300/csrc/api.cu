@@ -133,8 +133,10 @@ struct lbm_ctx {
   lbm::Feq81 feq_in[2]{};
   lbm::Feq81 feq_in_own[2]{};  // feq_in with direction i in the slot of -c_i (AA own layout)
   long long launches = 0;
-  // Staged host transfers: copy streams, slot events, kRing input then kRing output slots.
-  cudaStream_t xfer_in = nullptr, xfer_out = nullptr;
+  // Staged host transfers: copy streams, a stream for the initialisation of arriving slabs
+  // (it overlaps the steps and moments of earlier ones), slot events, kRing input then kRing
+  // output slots.
+  cudaStream_t xfer_in = nullptr, xfer_out = nullptr, init_stream = nullptr;
   cudaEvent_t in_ready[kRing] = {}, in_free[kRing] = {}, out_ready[kRing] = {}, out_free[kRing] = {};
   cudaEvent_t mark = nullptr;
   double* d_stage = nullptr;
@@ -311,6 +313,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   }
   e = cudaStreamCreateWithFlags(&ctx->xfer_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->init_stream, cudaStreamNonBlocking);
   for (int k = 0; k < kRing && e == cudaSuccess; ++k) {
     e = cudaEventCreateWithFlags(&ctx->in_ready[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->in_free[k], cudaEventDisableTiming);
@@ -543,25 +546,26 @@ cudaError_t stage_in(lbm_ctx* ctx, int k, double* const host[3]) {
 }
 
 // Equilibrium initialisation of slab k from its input slot (buffer 0), and the zero-gradient
-// ghosts of its planes when a step follows.
+// ghosts of its planes when a step follows, on the init stream; in_free[k % kRing] marks its end.
 cudaError_t init_slab(lbm_ctx* ctx, int k, bool fill_ghosts) {
   const int r = k % kRing;
   const Slab sl = slab_at(ctx, k);
   const long long n = ctx->sites / 2, M = ctx->slab_m, nxy = static_cast<long long>(ctx->cfg.nx) * ctx->cfg.ny;
   double* slot = stage_slot(ctx, 0, k);
-  cudaError_t e = cudaStreamWaitEvent(ctx->stream, ctx->in_ready[r], 0);
+  cudaStream_t s = ctx->init_stream;
+  cudaError_t e = cudaStreamWaitEvent(s, ctx->in_ready[r], 0);
   for (int sub = 0; sub < 2 && e == cudaSuccess; ++sub) {
     e = lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], slot + sub * M,
-                         slot + (2 + sub) * M, slot + (8 + sub) * M, sub * n + sl.z0 * nxy, sl.m, 2 * M, ctx->stream,
+                         slot + (2 + sub) * M, slot + (8 + sub) * M, sub * n + sl.z0 * nxy, sl.m, 2 * M, s,
                          ctx->d_flag, 0);
     ++ctx->launches;
   }
   for (int face = 0; face < 2 && e == cudaSuccess && fill_ghosts; ++face) {
     if (!ctx->zero_grad[face]) continue;
-    e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, ctx->stream, sl.z0, sl.z1);
+    e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, s, sl.z0, sl.z1);
     ++ctx->launches;
   }
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->in_free[r], ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->in_free[r], s);
   return e;
 }
 
@@ -603,18 +607,18 @@ cudaError_t slab_step(lbm_ctx* ctx, int k) {
                                     ctx->stream);
 }
 
-// The copy streams start after the work already queued on the context's stream ...
+// The copy and init streams start after the work already queued on the context's stream ...
 cudaError_t fork_copies(lbm_ctx* ctx) {
   cudaError_t e = cudaEventRecord(ctx->mark, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer_in, ctx->mark, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->xfer_out, ctx->mark, 0);
+  for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out, ctx->init_stream})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ctx->mark, 0);
   return e;
 }
 
-// ... and the context's stream continues after their last copy.
+// ... and the context's stream continues after their last copy or kernel.
 cudaError_t join_copies(lbm_ctx* ctx) {
   cudaError_t e = cudaSuccess;
-  for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out}) {
+  for (cudaStream_t xs : {ctx->init_stream, ctx->xfer_in, ctx->xfer_out}) {
     if (e == cudaSuccess) e = cudaEventRecord(ctx->mark, xs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->mark, 0);
   }
@@ -653,9 +657,12 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
   for (int j = 0; j < N; ++j) {
     LBM_CK(ctx, init_slab(ctx, j, n == 1));
     if (j + kRing < N) LBM_CK(ctx, stage_in(ctx, j + kRing, in));
+    // what follows needs init up to slab j (and no further): wait for in_free[j % kRing]
     if (n == 0) {
+      LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
       LBM_CK(ctx, moments_out(ctx, j, q++, ctx->buf[0], lbm::kLayoutPlain, out));
-    } else if (n == 1) {
+    } else if (n == 1 && next < order.size() && need[order[next]] <= j) {
+      LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
       for (; next < order.size() && need[order[next]] <= j; ++next) {
         LBM_CK(ctx, slab_step(ctx, order[next]));
         LBM_CK(ctx, moments_out(ctx, order[next], q++, ctx->buf[1], lbm::kLayoutPlain, out));
@@ -664,6 +671,8 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
   }
   ctx->initialized = true;
   if (n >= 2) {
+    LBM_CK(ctx, cudaEventRecord(ctx->mark, ctx->init_stream));
+    LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->mark, 0));
     st = run_steps(ctx, n - 1);
     if (st != LBM_OK) return st;
     for (int face = 0; face < 2; ++face) {
@@ -890,7 +899,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (!valid(ctx)) return LBM_EINVAL;
   {
     DeviceGuard dg(ctx->device);
-    for (cudaStream_t xs : {ctx->stream, ctx->xfer_in, ctx->xfer_out})
+    for (cudaStream_t xs : {ctx->stream, ctx->xfer_in, ctx->xfer_out, ctx->init_stream})
       if (xs) cudaStreamSynchronize(xs);
     for (int b = 0; b < 2; ++b)
       if (ctx->buf[b]) cudaFree(ctx->buf[b]);
@@ -900,7 +909,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
-    for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out})
+    for (cudaStream_t xs : {ctx->xfer_in, ctx->xfer_out, ctx->init_stream})
       if (xs) cudaStreamDestroy(xs);
     for (int k = 0; k < kRing; ++k)
       for (cudaEvent_t ev : {ctx->in_ready[k], ctx->in_free[k], ctx->out_ready[k], ctx->out_free[k]})

@@ -254,19 +254,37 @@ __device__ __forceinline__ void site_moments_dw(const Geometry& g, const Lattice
     jz = {dz, 0.0f};
     e = dw_add(Dw{tab.theta0x3_dw[0], tab.theta0x3_dw[1]}, de);
   } else {
-    rho = jx = jy = jz = e = Dw{0.0f, 0.0f};
-    static_for<kShells>([&](auto Sc) {
-      constexpr int s = decltype(Sc)::value;
+    // Cascaded sums (Sum2 and Dot2 of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26, 2005):
+    // the running sum stays one float and the rounding error of every addition (TwoSum) and
+    // product (TwoProd) collects in a second float; the pair is as accurate as a sum in twice
+    // the working precision, at about half the operations of a renormalised double-word sum.
+    float pr = sr[0], px = 0.0f, py = 0.0f, pz = 0.0f, pe = 0.0f;
+    float qr = 0.0f, qx = 0.0f, qy = 0.0f, qz = 0.0f, qe = 0.0f;
+    static_for<kShells - 1>([&](auto Sc) {
+      constexpr int s = decltype(Sc)::value + 1;
       constexpr float c2 = static_cast<float>(rd3q81::kShellC2[s]);  // multiples of 1/4: exact
-      rho = dw_add(rho, sr[s]);
-      jx = dw_add(jx, sx[s]);
-      jy = dw_add(jy, sy[s]);
-      jz = dw_add(jz, sz[s]);
-      if constexpr (c2 != 0.0f) {
-        const Dw p = two_prod(c2, sr[s]);
-        e = dw_add(dw_add(e, p.hi), p.lo);
-      }
+      Dw t = two_sum(pr, sr[s]);
+      pr = t.hi;
+      qr = __fadd_rn(qr, t.lo);
+      t = two_sum(px, sx[s]);
+      px = t.hi;
+      qx = __fadd_rn(qx, t.lo);
+      t = two_sum(py, sy[s]);
+      py = t.hi;
+      qy = __fadd_rn(qy, t.lo);
+      t = two_sum(pz, sz[s]);
+      pz = t.hi;
+      qz = __fadd_rn(qz, t.lo);
+      const Dw h = two_prod(c2, sr[s]);
+      t = two_sum(pe, h.hi);
+      pe = t.hi;
+      qe = __fadd_rn(qe, __fadd_rn(t.lo, h.lo));
     });
+    rho = fast_two_sum(pr, qr);
+    jx = two_sum(px, qx);  // momenta may cancel to below their error term
+    jy = two_sum(py, qy);
+    jz = two_sum(pz, qz);
+    e = fast_two_sum(pe, qe);
   }
 }
 
