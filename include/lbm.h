@@ -164,8 +164,11 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n);
 lbm_status lbm_advance_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, long long n,
                               double* rho_out, double* u_out, double* theta_out, int on_device);
 
-/* rho, u, theta of the stored (post-collision) state, computed in FP64 (Eq. (conslaws));
- * layout as for lbm_init.  Synchronises the stream; returns LBM_EUNSTABLE (after writing
+/* rho, u, theta of the stored (post-collision) state (Eq. (conslaws)), returned in FP64;
+ * layout as for lbm_init.  FP64 storage sums and divides in FP64.  FP32/FP16/BF16 storage sums
+ * each velocity shell in FP32, then combines the shells, divides and forms theta in double-word
+ * (float + float) arithmetic: relative error ~1e-14 beyond the FP32 shell sums, at FP32 speed
+ * (this GPU runs FP64 at a small fraction of its FP32 rate).  Synchronises the stream; returns LBM_EUNSTABLE (after writing
  * the fields) if any step so far was flagged. */
 lbm_status lbm_moments(lbm_ctx* ctx, double* rho, double* u, double* theta, int on_device);
 
