@@ -34,9 +34,10 @@ read against the paper line by line:
 * ``diagnostics``         Sec. IV C: mean kinetic energy and mean enstrophy (curl by central
                           differences on each sublattice).
 * ``fill_ghosts_x``       Boundary layers in x.  The paper names its own boundary
-                          conditions without formulas; this oracle implements the three the
+                          conditions without formulas; this oracle implements the four the
                           library offers (periodic, zero-gradient outflow, equilibrium
-                          inflow), each defined in its docstring.
+                          inflow, and the bounce-back wall of the Sod setup in Sec. IV A,
+                          applied in ``stream``), each defined in its docstring.
 
 Parity pins (tests/test_oracle_*.py): lattice identities in exact arithmetic, the paper's
 printed moment-error column, W~ against its closed-form generating function, equilibrium
@@ -419,7 +420,9 @@ def fill_ghosts_x(fs: np.ndarray, bc_lo, bc_hi, feq_lo=None, feq_hi=None, width:
       "zero_gradient" every ghost layer copies all populations of the nearest interior
                       layer of the same sublattice (same y, z) -- an outflow face;
       "eq_inflow"     every ghost site holds feq(rho_in, u_in, theta_in) (``feq_lo`` /
-                      ``feq_hi``: the 81 values, identical on both sublattices).
+                      ``feq_hi``: the 81 values, identical on both sublattices);
+      "bounce_back"   a solid wall: the ghosts are never used (NaN here), ``stream`` returns
+                      every population whose link crosses the wall to its own site.
     """
     q, nz, ny, nx = fs.shape
     ext = np.empty((q, nz, ny, nx + 2 * width))
@@ -437,6 +440,8 @@ def fill_ghosts_x(fs: np.ndarray, bc_lo, bc_hi, feq_lo=None, feq_hi=None, width:
             ext[..., sl] = edge
         elif kind == "eq_inflow":
             ext[..., sl] = np.asarray(feq, dtype=np.float64).reshape(q, 1, 1, 1)
+        elif kind == "bounce_back":
+            ext[..., sl] = np.nan
         else:
             raise ValueError(f"unknown boundary kind {kind!r}")
     return ext
@@ -449,11 +454,19 @@ def stream(f: np.ndarray, bc=("periodic", "periodic"), feq_in=(None, None),
 
     y and z are periodic; ``bc`` gives the kinds of the -x and +x faces (see
     ``fill_ghosts_x``); ``feq_in`` the inflow populations of those faces (or None).
+
+    A "bounce_back" face is a solid wall (Sec. IV A: the Sod tube's x ends).  The fluid is the
+    index range 0 <= x < nx of both sublattices; a population f*_j leaving site n along a link
+    whose end has an x index outside that range comes back to n reversed, so
+    f_i(n, t + 1) = f*_{-i}(n, t) wherever the source n - d of the pull lies outside.  Every
+    population is kept (a permutation of the values), so mass and energy are conserved exactly.
     """
     lat = lat or velocity_set()
     width = 4
     ext = [fill_ghosts_x(f[s], bc[0], bc[1], feq_in[0], feq_in[1], width) for s in (0, 1)]
     nx = f.shape[-1]
+    opp = [int(np.flatnonzero(np.all(lat.h == -lat.h[i], axis=1))[0]) for i in range(lat.q)]
+    xs = np.arange(nx)
     out = np.empty_like(f)
     for s in (0, 1):
         for i in range(lat.q):
@@ -463,6 +476,10 @@ def stream(f: np.ndarray, bc=("periodic", "periodic"), feq_in=(None, None),
             a = a[:, :, width - dx:width - dx + nx]        # out[x] = ext[x + width - dx]
             a = np.roll(a, shift=(dz, dy), axis=(0, 1))    # out[n] = src[n - d] in y, z
             out[s, i] = a
+            # walls: the source x index is x - dx
+            cut = ((xs - dx < 0) & (bc[0] == "bounce_back")) | ((xs - dx >= nx) & (bc[1] == "bounce_back"))
+            if cut.any():
+                out[s, i][..., cut] = f[s, opp[i]][..., cut]
     return out
 
 
@@ -629,8 +646,8 @@ def step(f: np.ndarray, tau: float, bc_x=(("periodic",), ("periodic",)),
          collision: str = "bgk") -> np.ndarray:
     """One time step: boundary fill, pull streaming, moments, equilibrium, collision.
 
-    ``bc_x`` holds the -x and +x face specs: ("periodic",), ("zero_gradient",) or
-    ("eq_inflow", rho, ux, uy, uz, theta).  ``eq`` selects the equilibrium: "series" (App. B)
+    ``bc_x`` holds the -x and +x face specs: ("periodic",), ("zero_gradient",),
+    ("bounce_back",) or ("eq_inflow", rho, ux, uy, uz, theta).  ``eq`` selects the equilibrium: "series" (App. B)
     or "entropic" (the exact minimiser of Sec. III).  ``collision`` is "bgk" (alpha = 2) or
     "entropic" (alpha the root of Eq. (delH) per site; needs eq="entropic")."""
     lat = lat or velocity_set()
