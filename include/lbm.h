@@ -70,7 +70,12 @@ typedef enum {
   LBM_BC_PERIODIC = 0,      /* wrap-around; the opposite face must be periodic too */
   LBM_BC_ZERO_GRADIENT = 1, /* outflow: ghost sites copy the nearest interior site of the
                                same sublattice (all 81 populations) before every step */
-  LBM_BC_EQ_INFLOW = 2      /* ghost sites hold f~eq(rho, u, theta) of the face's state */
+  LBM_BC_EQ_INFLOW = 2,     /* ghost sites hold f~eq(rho, u, theta) of the face's state */
+  LBM_BC_BOUNCE_BACK = 3    /* solid wall (the Sod tube's x ends, Sec. IV A): a population whose
+                               link from a fluid site would end outside the fluid index range
+                               0 <= x < nx comes back to that site one step later with the reversed
+                               velocity, f_-i(x, t+1) = f*_i(x, t).  Keeps every population, so mass
+                               and energy are conserved exactly.  Not available to served cases. */
 } lbm_bc_kind;
 
 typedef enum {

@@ -20,7 +20,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_EBUS
 STATUS_NAMES = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSTABLE",
                 5: "LBM_ETIMEOUT", 6: "LBM_EBUSY", 7: "LBM_ENOTFOUND"}
 LBM_RD3Q81 = 1
-LBM_BC_PERIODIC, LBM_BC_ZERO_GRADIENT, LBM_BC_EQ_INFLOW = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_ZERO_GRADIENT, LBM_BC_EQ_INFLOW, LBM_BC_BOUNCE_BACK = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16_OFFSET, LBM_BF16_OFFSET = 0, 1, 2, 3
 LBM_EQ_SERIES, LBM_EQ_ENTROPIC, LBM_EQ_SERIES_EXACT_W = 0, 1, 2
 EQUILIBRIUM = {"series": LBM_EQ_SERIES, "entropic": LBM_EQ_ENTROPIC, "series_exact_w": LBM_EQ_SERIES_EXACT_W}
@@ -132,7 +132,8 @@ def _ptr(a, writable: bool = False):
 def make_config(nx: int, ny: int, nz: int, tau: float, storage="f32", faces=None, fp64_moments=False,
                 stream=None, equilibrium="series", collision="bgk", streaming="pingpong") -> lbm_config:
     """Builds an lbm_config.  ``faces``: up to 6 face specs (-x, +x, -y, +y, -z, +z), each
-    "periodic", "zero_gradient" or ("eq_inflow", rho, ux, uy, uz, theta); default periodic.
+    "periodic", "zero_gradient", "bounce_back" or ("eq_inflow", rho, ux, uy, uz, theta); default
+    periodic.
     ``stream``: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
     ``equilibrium``: "series" (App. B), "series_exact_w" (App. B with the exact weights W(theta))
     or "entropic" (Sec. III, exact).
@@ -155,7 +156,8 @@ def make_config(nx: int, ny: int, nz: int, tau: float, storage="f32", faces=None
             spec = (spec,)
         kind = spec[0]
         b.kind = {"periodic": LBM_BC_PERIODIC, "zero_gradient": LBM_BC_ZERO_GRADIENT,
-                  "eq_inflow": LBM_BC_EQ_INFLOW}.get(kind, -1) if isinstance(kind, str) else int(kind)
+                  "eq_inflow": LBM_BC_EQ_INFLOW, "bounce_back": LBM_BC_BOUNCE_BACK}.get(kind, -1) \
+            if isinstance(kind, str) else int(kind)
         if kind == "eq_inflow":
             b.rho, b.ux, b.uy, b.uz, b.theta = (float(v) for v in spec[1:6])
     if stream is None:

@@ -66,7 +66,7 @@ lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
            LBM_EINVAL;
   for (int f = 0; f < 6; ++f) {
     const lbm_bc& b = cfg->face[f];
-    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_EQ_INFLOW) return *why = "unknown boundary kind", LBM_EINVAL;
+    if (b.kind < LBM_BC_PERIODIC || b.kind > LBM_BC_BOUNCE_BACK) return *why = "unknown boundary kind", LBM_EINVAL;
     if (f >= 2 && b.kind != LBM_BC_PERIODIC)
       return *why = "only the x faces may be non-periodic in this version", LBM_EINVAL;
     if (b.kind == LBM_BC_EQ_INFLOW &&
@@ -130,6 +130,7 @@ struct lbm_ctx {
   bool initialized = false;
   bool zero_grad[2] = {false, false};
   bool inflow[2] = {false, false};
+  bool bounce[2] = {false, false};
   lbm::Feq81 feq_in[2]{};
   lbm::Feq81 feq_in_own[2]{};  // feq_in with direction i in the slot of -c_i (AA own layout)
   long long launches = 0;
@@ -263,6 +264,7 @@ lbm_status lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     const lbm_bc& b = cfg->face[face];
     ctx->zero_grad[face] = b.kind == LBM_BC_ZERO_GRADIENT;
     ctx->inflow[face] = b.kind == LBM_BC_EQ_INFLOW;
+    ctx->bounce[face] = b.kind == LBM_BC_BOUNCE_BACK;
     if (ctx->inflow[face]) {
       if (cfg->equilibrium == LBM_EQ_ENTROPIC)
         lbm::entropic_all<double>(b.rho, b.ux, b.uy, b.uz, b.theta, ctx->tab, ctx->feq_in[face].v);
@@ -391,8 +393,9 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long l
   static_assert(kGraphSteps % 2 == 0, "a captured run must return to its starting state");
   if (!ctx->aa) {
     for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
-      if (!ctx->zero_grad[face]) continue;
-      e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
+      if (ctx->zero_grad[face]) e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
+      else if (ctx->bounce[face]) e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[cur], face, 0, s);
+      else continue;
       ++*launches;
     }
     if (e != cudaSuccess) return e;
@@ -413,6 +416,8 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long l
     if (ctx->zero_grad[face]) e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, s);
     else if (ctx->inflow[face])
       e = lbm::launch_fill_inflow(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->feq_in_own[face], s);
+    else if (ctx->bounce[face])
+      e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 1, s);
     else continue;
     ++*launches;
   }
@@ -421,9 +426,12 @@ cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long l
   ++*launches;
   e = lbm::launch_stream_collide(ctx->storage, 0, step_mode(ctx), lbm::kStepAANeighbour, p, s);
   for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
-    if (!ctx->zero_grad[face] && !ctx->inflow[face]) continue;
-    e = lbm::launch_aa_ghost_push(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->zero_grad[face] ? 1 : 0,
-                                  ctx->feq_in[face], s);
+    if (ctx->bounce[face])
+      e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 2, s);
+    else if (ctx->zero_grad[face] || ctx->inflow[face])
+      e = lbm::launch_aa_ghost_push(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->zero_grad[face] ? 1 : 0,
+                                    ctx->feq_in[face], s);
+    else continue;
     ++*launches;
   }
   return e;
@@ -641,18 +649,26 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
   if (st != LBM_OK) return st;
   LBM_CK(ctx, fork_copies(ctx));
   for (int k = 0; k < N && k < kRing; ++k) LBM_CK(ctx, stage_in(ctx, k, in));
-  // n == 1: need[k] = the last slab, in init order, holding a plane within kReach of slab k
-  std::vector<int> need(N, 0), order(N);
-  for (int k = 0; k < N; ++k) {
-    order[k] = k;
+  // n == 1: need[k] = the last slab, in init order, holding a plane within kReach of slab k.  A
+  // bounce-back wall's ghosts on slab k's planes read fluid sites within that reach (they run once
+  // need[k] is initialised), and slab k's step reads the ghosts of every slab within its reach:
+  // with walls a step waits for step_need[k] = max(need[k'] : k' within reach of k).
+  std::vector<int> need(N, 0), step_need(N, 0), order(N), fill_order(N);
+  auto slabs_within_reach = [&](int k, auto&& fn) {
     const Slab sl = slab_at(ctx, k);
-    for (int z = sl.z0 - rd3q81::kReach; z < sl.z1 + rd3q81::kReach; ++z) {
-      const int zz = ((z % ctx->cfg.nz) + ctx->cfg.nz) % ctx->cfg.nz;
-      need[k] = std::max(need[k], zz / ctx->slab_planes);
-    }
+    for (int z = sl.z0 - rd3q81::kReach; z < sl.z1 + rd3q81::kReach; ++z)
+      fn((((z % ctx->cfg.nz) + ctx->cfg.nz) % ctx->cfg.nz) / ctx->slab_planes);
+  };
+  for (int k = 0; k < N; ++k) slabs_within_reach(k, [&](int k2) { need[k] = std::max(need[k], k2); });
+  const bool walls = ctx->bounce[0] || ctx->bounce[1];
+  for (int k = 0; k < N; ++k) {
+    order[k] = fill_order[k] = k;
+    step_need[k] = need[k];
+    if (walls) slabs_within_reach(k, [&](int k2) { step_need[k] = std::max(step_need[k], need[k2]); });
   }
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return need[a] < need[b]; });
-  size_t next = 0;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return step_need[a] < step_need[b]; });
+  std::stable_sort(fill_order.begin(), fill_order.end(), [&](int a, int b) { return need[a] < need[b]; });
+  size_t next = 0, next_fill = 0;
   long long q = 0;
   for (int j = 0; j < N; ++j) {
     LBM_CK(ctx, init_slab(ctx, j, n == 1));
@@ -661,9 +677,19 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
     if (n == 0) {
       LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
       LBM_CK(ctx, moments_out(ctx, j, q++, ctx->buf[0], lbm::kLayoutPlain, out));
-    } else if (n == 1 && next < order.size() && need[order[next]] <= j) {
+    } else if (n == 1 && ((next < order.size() && step_need[order[next]] <= j) ||
+                          (walls && next_fill < fill_order.size() && need[fill_order[next_fill]] <= j))) {
       LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
-      for (; next < order.size() && need[order[next]] <= j; ++next) {
+      for (; walls && next_fill < fill_order.size() && need[fill_order[next_fill]] <= j; ++next_fill) {
+        const Slab sl = slab_at(ctx, fill_order[next_fill]);
+        for (int face = 0; face < 2; ++face) {
+          if (!ctx->bounce[face]) continue;
+          LBM_CK(ctx, lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 0, ctx->stream,
+                                              sl.z0, sl.z1));
+          ++ctx->launches;
+        }
+      }
+      for (; next < order.size() && step_need[order[next]] <= j; ++next) {
         LBM_CK(ctx, slab_step(ctx, order[next]));
         LBM_CK(ctx, moments_out(ctx, order[next], q++, ctx->buf[1], lbm::kLayoutPlain, out));
       }
@@ -676,8 +702,13 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
     st = run_steps(ctx, n - 1);
     if (st != LBM_OK) return st;
     for (int face = 0; face < 2; ++face) {
-      if (!ctx->zero_grad[face]) continue;
-      LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
+      if (ctx->zero_grad[face])
+        LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
+      else if (ctx->bounce[face])
+        LBM_CK(ctx, lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], face, 0,
+                                            ctx->stream));
+      else
+        continue;
       ++ctx->launches;
     }
     for (int k = 0; k < N; ++k) {

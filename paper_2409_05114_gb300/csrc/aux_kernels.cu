@@ -407,6 +407,46 @@ __global__ void inflow_kernel(Geometry g, LatticeTables tab, S* buf, int face, F
   for (int l = 0; l < rd3q81::kReach; ++l) encode<S>(buf + row + x0 + l, feq.v[i], tab.wdir[i]);
 }
 
+// Bounce-back wall on one x face (LBM_BC_BOUNCE_BACK), thread per (sub, i, z, y) ghost row, z in
+// [z0, z0 + nzr).  Ghost (s', g) of direction i is pulled by exactly one site p = (push_d[s'][i][3],
+// g - push_d[s'][i][0..2]).  Where p is a fluid site (0 <= x < nx), the link p -> g leaves the
+// fluid, and the wall returns p's own population of the opposite direction to p:
+//   mode 0 (ping-pong, before a step):        ghost slot i      <- p slot opp(i);
+//   mode 1 (AA own layout, before a neighbour step, which reads ghost slot opp(i) for f_i):
+//                                             ghost slot opp(i) <- p slot i (= f*_opp(i) of p);
+//   mode 2 (AA, after that neighbour step, which pushed f*_opp(i) of p into ghost slot opp(i)):
+//                                             p slot i          <- ghost slot opp(i).
+// A ghost row writes only ghost elements (modes 0, 1) or only the (p, i) slots that no neighbour
+// step wrote (mode 2); each such element belongs to one thread.  Offset storage copies the stored
+// offsets: i and opp(i) share their weight.
+template <class S>
+__global__ void bounce_back_kernel(Geometry g, LatticeTables tab, S* buf, int face, int mode, int z0, int nzr) {
+  const long long rows = 2LL * kQ * nzr * g.ny;
+  const long long k = static_cast<long long>(blockIdx.x) * kAuxBlock + threadIdx.x;
+  if (k >= rows) return;
+  const int y = static_cast<int>(k % g.ny);
+  const long long r = k / g.ny;
+  const int z = z0 + static_cast<int>(r % nzr);
+  const long long si = r / nzr;
+  const int sub = static_cast<int>(si / kQ), i = static_cast<int>(si % kQ);
+  const signed char* d = tab.push_d[sub][i];
+  const int py = wrap_idx(y - d[1], g.ny), pz = wrap_idx(z - d[2], g.nz);
+  const long long grow = sub * g.sub_stride + z * g.plane + static_cast<long long>(y) * g.pitch + g.xoff;
+  const long long prow = d[3] * g.sub_stride + pz * g.plane + static_cast<long long>(py) * g.pitch + g.xoff;
+  const long long si_i = i * g.dir_stride, si_o = tab.opp[i] * g.dir_stride;
+  for (int l = 0; l < rd3q81::kReach; ++l) {
+    const int gx = face == 0 ? -1 - l : g.nx + l;
+    const int px = gx - d[0];
+    if (px < 0 || px >= g.nx) continue;
+    if (mode == 0)
+      buf[grow + si_i + gx] = buf[prow + si_o + px];
+    else if (mode == 1)
+      buf[grow + si_o + gx] = buf[prow + si_i + px];
+    else
+      buf[prow + si_i + px] = buf[grow + si_o + gx];
+  }
+}
+
 // AA streaming, after a neighbour step: the populations a ghost site of this x face would have
 // pushed into the interior (the neighbour step runs on interior sites only).  Thread per
 // (sub, z, y, ghost layer).  Zero gradient: the ghost holds the nearest interior site's
@@ -555,6 +595,17 @@ cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf,
   const long long rows = 2LL * kQ * (z1 - z0) * g.ny;
   LBM_STORAGE_DISPATCH(storage, (zero_gradient_kernel<S><<<blocks_for(rows), kAuxBlock, 0, s>>>(
                                     g, static_cast<S*>(buf), face, z0, z1 - z0)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounce_back(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
+                               int mode, cudaStream_t s, int z0, int z1) {
+  if (z1 < 0) z1 = g.nz;
+  if (z0 < 0 || z1 > g.nz || mode < 0 || mode > 2) return cudaErrorInvalidValue;
+  if (z1 <= z0) return cudaSuccess;
+  const long long rows = 2LL * kQ * (z1 - z0) * g.ny;
+  LBM_STORAGE_DISPATCH(storage, (bounce_back_kernel<S><<<blocks_for(rows), kAuxBlock, 0, s>>>(
+                                    g, tab, static_cast<S*>(buf), face, mode, z0, z1 - z0)));
   return cudaGetLastError();
 }
 

@@ -170,6 +170,11 @@ cudaError_t launch_fill_inflow(int storage, const Geometry& g, const LatticeTabl
 // Zero-gradient ghost layers of one x face, for the z planes [z0, z1) (z1 < 0: through nz).
 cudaError_t launch_fill_zero_gradient(int storage, const Geometry& g, void* buf, int face, cudaStream_t s,
                                       int z0 = 0, int z1 = -1);
+// Bounce-back wall on one x face for the z planes [z0, z1) (z1 < 0: through nz).  mode 0: ghost
+// fill before a ping-pong step; 1: ghost fill in the AA own layout before a neighbour step; 2: after
+// that neighbour step, what the wall returns into the fluid sites' slots.
+cudaError_t launch_bounce_back(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
+                               int mode, cudaStream_t s, int z0 = 0, int z1 = -1);
 // AA: after a neighbour step, what the ghost sites of one x face push into the interior.
 cudaError_t launch_aa_ghost_push(int storage, const Geometry& g, const LatticeTables& tab, void* buf, int face,
                                  int zero_grad, const Feq81& feq, cudaStream_t s);

@@ -506,6 +506,11 @@ lbm_status lbm_submit(lbm_server* s, const lbm_config* cfg, const double* rho, c
     s->err = why;
     return LBM_EINVAL;
   }
+  if (cfg->face[0].kind == LBM_BC_BOUNCE_BACK || cfg->face[1].kind == LBM_BC_BOUNCE_BACK) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "served cases take periodic, zero-gradient or equilibrium-inflow faces";
+    return LBM_EINVAL;
+  }
   if (cfg->storage == LBM_F64 || cfg->fp64_moments || cfg->equilibrium != LBM_EQ_SERIES) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments and the series equilibrium";

@@ -75,23 +75,27 @@ def positions(nx: int, ny: int, nz: int):
     return tuple(np.stack([a, a + 0.5]) for a in (x, y, z))
 
 
-def sod(nx: int = 512, ny: int = 4, nz: int = 4, tau_lb: float = 0.6, steps: int = 200) -> Workload:
+def sod(nx: int = 512, ny: int = 4, nz: int = 4, tau_lb: float = 0.6, steps: int = 200,
+        walls: bool = False) -> Workload:
     """Left half rho = 1, theta = theta0; right half rho = 0.125, theta = 0.8 theta0; u = 0.
-    The interface is at x = nx/2 (physical position)."""
+    The interface is at x = nx/2 (physical position).  x faces zero-gradient, or with ``walls``
+    bounce-back as in the paper's Sod setup (Sec. IV A: 4000 x 8 x 8, periodic y and z)."""
     x, _, _ = positions(nx, ny, nz)
     left = x < nx / 2.0
     rho = np.where(left, 1.0, 0.125)
     theta = np.where(left, THETA0, 0.8 * THETA0)
     u = np.zeros((3,) + rho.shape)
-    return Workload("sod", nx, ny, nz, tau_lb, steps, rho, u, theta,
-                    ["zero_gradient", "zero_gradient"] + ["periodic"] * 4)
+    x_face = "bounce_back" if walls else "zero_gradient"
+    return Workload("sod_walls" if walls else "sod", nx, ny, nz, tau_lb, steps, rho, u, theta,
+                    [x_face, x_face] + ["periodic"] * 4)
 
 
 def shock_tube(nx: int = 512, ny: int = 4, nz: int = 4, rho_right: float = 0.125, theta_right: float = 0.8,
-               tau_lb: float = 0.6, steps: int = 200) -> Workload:
+               tau_lb: float = 0.6, steps: int = 200, walls: bool = False) -> Workload:
     """Sod-type tube: left rho = 1, theta = theta0; right rho = rho_right,
-    theta = theta_right * theta0; u = 0; interface at x = nx/2; zero-gradient x faces."""
-    wl = sod(nx, ny, nz, tau_lb, steps)
+    theta = theta_right * theta0; u = 0; interface at x = nx/2; zero-gradient x faces, or
+    bounce-back walls with ``walls``."""
+    wl = sod(nx, ny, nz, tau_lb, steps, walls)
     x, _, _ = positions(nx, ny, nz)
     left = x < nx / 2.0
     wl.rho = np.where(left, 1.0, rho_right)
