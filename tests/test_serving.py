@@ -123,7 +123,10 @@ def test_served_case_matches_oracle(B):
 def test_admission_respects_budget(B):
     wl = W.taylor_green(32)
     cfg = B.make_config(wl.nx, wl.ny, wl.nz, 0.01, "f32")
-    one = 2 * 2 * 81 * wl.nx * wl.ny * wl.nz * 4            # two buffers, both sublattices
+    # a served case holds two population buffers; lbm_footprint adds a context's scratch and
+    # staging to those, so it bounds one case's footprint from above (the library pads rows to
+    # whole x tiles, so the buffers are not 81 x sites x 4 bytes exactly)
+    one = B.lbm_footprint(cfg)
     items = [(wl, "f32", 0.01, 10)] * 3
     results, stats = _serve(B, items, budget=int(one * 1.5))
     assert all(st == B.LBM_OK for st, _ in results)
