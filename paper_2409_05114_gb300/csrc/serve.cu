@@ -64,8 +64,11 @@ __device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, 
     site_update<S, false, 1>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
 }
 
-// Step k of the current tick for every resident case.  Grid: persistent (SMs x resident
-// blocks); block b handles tiles b, b + gridDim.x, ...  No block waits on another.
+// Step k of the current tick for the resident cases of one storage type S (one kernel per type,
+// so each holds one storage's site update: a kernel with all three overflowed the instruction
+// cache).  Grid: persistent (SMs x resident blocks); block b handles tiles b, b + gridDim.x, ...
+// No block waits on another.
+template <class S>
 __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
                                                                long long total_tiles, int k, const LatticeTables tab) {
   __shared__ long long s_first[kMaxServerCases];
@@ -80,13 +83,19 @@ __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc
     const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
     if (t >= n) continue;
     const int par = (cd.parity + k) & 1;
-    switch (cd.storage) {
-      case kF32: served_site<float>(cd, sub, static_cast<int>(t), par, tab); break;
-      case kF16Off: served_site<__half>(cd, sub, static_cast<int>(t), par, tab); break;
-      default: served_site<__nv_bfloat16>(cd, sub, static_cast<int>(t), par, tab); break;
-    }
+    served_site<S>(cd, sub, static_cast<int>(t), par, tab);
   }
 }
+
+// Resident cases grouped by storage type: the case table lists the FP32 cases, then FP16, then
+// BF16; each group's tiles are numbered from 0 for its own kernel.
+constexpr int kStorageGroups = 3;
+constexpr int kGroupStorage[kStorageGroups] = {kF32, kF16Off, kBF16Off};
+struct TickPlan {
+  int first[kStorageGroups] = {0, 0, 0};    // first case of the group in the table
+  int count[kStorageGroups] = {0, 0, 0};
+  long long tiles[kStorageGroups] = {0, 0, 0};
+};
 
 template <class T>
 __device__ __forceinline__ void copy_edge(T* buf, const CaseDesc& cd, long long row, int face) {
@@ -285,7 +294,7 @@ lbm_status admit_some(lbm_server* s) {
   }
 }
 
-cudaGraphExec_t tick_graph(lbm_server* s, int ncases, long long total_tiles, long long total_rows, int K) {
+cudaGraphExec_t tick_graph(lbm_server* s, int ncases, const TickPlan& plan, long long total_rows, int K) {
   auto key = std::make_pair(s->version, K);
   auto it = s->graphs.find(key);
   if (it != s->graphs.end()) return it->second;
@@ -294,13 +303,24 @@ cudaGraphExec_t tick_graph(lbm_server* s, int ncases, long long total_tiles, lon
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, std::max<long long>(total_tiles, 1)));
   for (int k = 0; ok && k < K; ++k) {
     if (total_rows > 0) {
       const int zb = static_cast<int>(std::min<long long>((total_rows + 255) / 256, 4096));
       served_zero_gradient_kernel<<<zb, 256, 0, cap>>>(s->d_cases, ncases, total_rows, k);
     }
-    served_step_kernel<<<grid, kScBlock, 0, cap>>>(s->d_cases, ncases, total_tiles, k, s->tab);
+    for (int gi = 0; gi < kStorageGroups; ++gi) {
+      if (plan.count[gi] == 0) continue;
+      const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, plan.tiles[gi]));
+      const CaseDesc* d = s->d_cases + plan.first[gi];
+      switch (kGroupStorage[gi]) {
+        case kF32: served_step_kernel<float><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab); break;
+        case kF16Off:
+          served_step_kernel<__half><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab);
+          break;
+        default:
+          served_step_kernel<__nv_bfloat16><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab);
+      }
+    }
   }
   if (ok) ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
   if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -371,10 +391,21 @@ lbm_status run_tick(lbm_server* s) {
   }
   if (s->active.empty()) return LBM_OK;
   const int ncases = static_cast<int>(s->active.size());
-  long long total_tiles = 0, total_rows = 0, min_left = s->active[0].steps_left;
+  long long total_rows = 0, min_left = s->active[0].steps_left;
+  TickPlan plan;
+  std::vector<int> order;  // active cases grouped by storage type
+  for (int gi = 0; gi < kStorageGroups; ++gi) {
+    plan.first[gi] = static_cast<int>(order.size());
+    for (int c = 0; c < ncases; ++c)
+      if (s->active[c].req->cfg.storage == kGroupStorage[gi]) order.push_back(c);
+    plan.count[gi] = static_cast<int>(order.size()) - plan.first[gi];
+  }
+  if (static_cast<int>(order.size()) != ncases) return set_fatal(s, "a resident case has an unserved storage type");
   for (int c = 0; c < ncases; ++c) {
-    Resident& a = s->active[c];
+    Resident& a = s->active[order[c]];
     CaseDesc& d = s->h_cases[c];
+    int gi = 0;
+    while (gi + 1 < kStorageGroups && c >= plan.first[gi + 1]) ++gi;
     d.g = a.g;
     d.buf[0] = a.buf[0];
     d.buf[1] = a.buf[1];
@@ -384,8 +415,8 @@ lbm_status run_tick(lbm_server* s) {
     d.parity = a.parity;
     const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
     d.tiles_sub = static_cast<int>((n + kScBlock - 1) / kScBlock);
-    d.tile0 = total_tiles;
-    total_tiles += 2LL * d.tiles_sub;
+    d.tile0 = plan.tiles[gi];
+    plan.tiles[gi] += 2LL * d.tiles_sub;
     d.zg_face[0] = a.zg[0];
     d.zg_face[1] = a.zg[1];
     d.rows_face = 2LL * kQ * a.g.nz * a.g.ny;
@@ -395,11 +426,13 @@ lbm_status run_tick(lbm_server* s) {
   }
   const int K = static_cast<int>(std::min<long long>(kTickSteps, min_left));
   SRV_CK(s, cudaMemcpyAsync(s->d_cases, s->h_cases, sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, s->compute));
-  cudaGraphExec_t g = tick_graph(s, ncases, total_tiles, total_rows, K);
+  cudaGraphExec_t g = tick_graph(s, ncases, plan, total_rows, K);
   if (!g) return set_fatal(s, "CUDA graph capture of a serving tick failed");
   SRV_CK(s, cudaGraphLaunch(g, s->compute));
   ++s->stats.graph_launches;
-  s->stats.kernel_launches += static_cast<long long>(K) * (total_rows > 0 ? 2 : 1);
+  int groups = 0;
+  for (int gi = 0; gi < kStorageGroups; ++gi) groups += plan.count[gi] > 0;
+  s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + groups);
   ++s->stats.ticks;
   SRV_CK(s, cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(unsigned int) * s->max_cases, cudaMemcpyDeviceToHost,
                             s->compute));
@@ -488,7 +521,7 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
   cudaMemset(s->d_flags, 0, sizeof(unsigned int) * max_cases);
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel, kScBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel<float>, kScBlock, 0);
   s->grid_blocks = std::max(1, sms * std::max(1, per_sm));
   s->worker = std::thread(worker_main, s);
   *out = s;
