@@ -42,7 +42,7 @@ struct CaseDesc {
   int parity;          // buffer holding the state at the start of the tick
   int tiles_sub;       // ceil(nx*ny*nz / kScBlock)
   int zg_face[2];      // zero-gradient at -x / +x
-  long long tile0;     // first packed tile
+  long long tile0;     // first packed tile of this case within its storage group's P half
   long long row0;      // first packed ghost row (zero-gradient faces)
   long long rows_face; // rows per zero-gradient face: 2 * 81 * nz * ny
 };
@@ -68,18 +68,20 @@ __device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, 
 // so each holds one storage's site update: a kernel with all three overflowed the instruction
 // cache).  Grid: persistent (SMs x resident blocks); block b handles tiles b, b + gridDim.x, ...
 // No block waits on another.
+// Tiles [0, half) are the P sublattice of every case of the group, [half, 2 half) the R
+// sublattice: blocks working side by side then mostly run one of the two compiled site updates.
 template <class S>
 __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
-                                                               long long total_tiles, int k, const LatticeTables tab) {
+                                                               long long half, int k, const LatticeTables tab) {
   __shared__ long long s_first[kMaxServerCases];
   for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].tile0;
   __syncthreads();
-  for (long long tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-    const int c = find_case(s_first, ncases, tile);
+  for (long long tile = blockIdx.x; tile < 2 * half; tile += gridDim.x) {
+    const int sub = tile >= half ? 1 : 0;
+    const long long ptile = tile - sub * half;
+    const int c = find_case(s_first, ncases, ptile);
     const CaseDesc& cd = cases[c];
-    const long long local = tile - cd.tile0;
-    const int sub = local >= cd.tiles_sub ? 1 : 0;
-    const long long t = (local - static_cast<long long>(sub) * cd.tiles_sub) * kScBlock + threadIdx.x;
+    const long long t = (ptile - cd.tile0) * kScBlock + threadIdx.x;
     const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
     if (t >= n) continue;
     const int par = (cd.parity + k) & 1;
@@ -94,7 +96,7 @@ constexpr int kGroupStorage[kStorageGroups] = {kF32, kF16Off, kBF16Off};
 struct TickPlan {
   int first[kStorageGroups] = {0, 0, 0};    // first case of the group in the table
   int count[kStorageGroups] = {0, 0, 0};
-  long long tiles[kStorageGroups] = {0, 0, 0};
+  long long tiles[kStorageGroups] = {0, 0, 0};  // P-sublattice tiles of the group (the R half is as many)
 };
 
 template <class T>
@@ -310,7 +312,7 @@ cudaGraphExec_t tick_graph(lbm_server* s, int ncases, const TickPlan& plan, long
     }
     for (int gi = 0; gi < kStorageGroups; ++gi) {
       if (plan.count[gi] == 0) continue;
-      const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, plan.tiles[gi]));
+      const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, 2 * plan.tiles[gi]));
       const CaseDesc* d = s->d_cases + plan.first[gi];
       switch (kGroupStorage[gi]) {
         case kF32: served_step_kernel<float><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab); break;
@@ -416,7 +418,7 @@ lbm_status run_tick(lbm_server* s) {
     const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
     d.tiles_sub = static_cast<int>((n + kScBlock - 1) / kScBlock);
     d.tile0 = plan.tiles[gi];
-    plan.tiles[gi] += 2LL * d.tiles_sub;
+    plan.tiles[gi] += d.tiles_sub;
     d.zg_face[0] = a.zg[0];
     d.zg_face[1] = a.zg[1];
     d.rows_face = 2LL * kQ * a.g.nz * a.g.ny;
