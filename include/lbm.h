@@ -160,12 +160,13 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n);
 /* lbm_init, lbm_step(n) and lbm_moments as one call: sets every site to f~eq of the fields
  * rho, u, theta, advances n >= 0 steps and writes the fields of the result to rho_out, u_out,
  * theta_out (layouts as lbm_init; the outputs may be the inputs).  The context keeps the state
- * afterwards, as after the three calls.  With page-locked host fields and ping-pong streaming
- * the work runs slab by slab in z: the host-to-device copy of later slabs, the kernels, and the
- * device-to-host copy of finished slabs overlap (both directions of the host link at once when
- * n <= 1; for n >= 2 the input overlaps initialisation and the output overlaps the last step).
- * Otherwise (device fields, pageable memory, AA streaming) the three calls run one after the
- * other.  Synchronises; LBM_EUNSTABLE as lbm_moments; LBM_EINVAL for NULL fields or n < 0. */
+ * afterwards, as after the three calls, and the fields are bitwise those of the three calls.
+ * With page-locked host fields the work runs slab by slab in z (ping-pong or AA streaming): the
+ * host-to-device copy of later slabs, the kernels, and the device-to-host copy of finished slabs
+ * overlap (both directions of the host link at once when n <= 1; for n >= 2 the input overlaps
+ * initialisation and the output overlaps the last step).  Device fields and pageable memory
+ * run the three calls one after the other.  Synchronises; LBM_EUNSTABLE as lbm_moments;
+ * LBM_EINVAL for NULL fields or n < 0. */
 lbm_status lbm_advance_fields(lbm_ctx* ctx, const double* rho, const double* u, const double* theta, long long n,
                               double* rho_out, double* u_out, double* theta_out, int on_device);
 

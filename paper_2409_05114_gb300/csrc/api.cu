@@ -379,61 +379,85 @@ int step_mode(const lbm_ctx* ctx) {
                                                           : lbm::kEqSeries;
 }
 
-// Issues one step on stream s and adds its launches to *launches.  Ping-pong: ghost fills,
-// then the fused kernel from buffer `cur` into the other.  AA (buffer 0, in place): from the
-// own layout, ghost fills in that layout, the neighbour step, then what the ghosts push into
-// the interior (leaves the pushed layout); from the pushed layout, the own-site step.
-cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long long* launches) {
+// The step that follows a stored state: ping-pong, or by AA layout (own -> neighbour step,
+// pushed -> own-site step).
+int step_kind(const lbm_ctx* ctx, int layout) {
+  return !ctx->aa ? lbm::kStepPingPong : layout == lbm::kLayoutAAPushed ? lbm::kStepAAOwn : lbm::kStepAANeighbour;
+}
+
+enum FillKinds { kFillZeroGrad = 1, kFillInflow = 2, kFillWalls = 4, kFillAll = 7 };
+
+// Boundary work before a step of `kind` from buffer `cur`, for the z planes [z0, z1) (z1 < 0:
+// all): zero-gradient and bounce-back ghosts of the source (ping-pong) or of the own layout (AA
+// neighbour step, which also refills the inflow ghosts it overwrites).  Ping-pong inflow ghosts
+// are constant, written at init; an own-site step reads no ghost.
+cudaError_t pre_step_fills(lbm_ctx* ctx, int cur, int kind, int kinds, cudaStream_t s, long long* launches,
+                           int z0 = 0, int z1 = -1) {
+  if (kind == lbm::kStepAAOwn) return cudaSuccess;
+  void* b = ctx->buf[kind == lbm::kStepPingPong ? cur : 0];
+  cudaError_t e = cudaSuccess;
+  for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
+    if (ctx->zero_grad[face] && (kinds & kFillZeroGrad))
+      e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, b, face, s, z0, z1);
+    else if (ctx->inflow[face] && kind == lbm::kStepAANeighbour && (kinds & kFillInflow))
+      e = lbm::launch_fill_inflow(ctx->storage, ctx->g, ctx->tab, b, face, ctx->feq_in_own[face], s);
+    else if (ctx->bounce[face] && (kinds & kFillWalls))
+      e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, b, face, kind == lbm::kStepPingPong ? 0 : 1, s, z0, z1);
+    else
+      continue;
+    ++*launches;
+  }
+  return e;
+}
+
+// The fused kernel of a step of `kind` from buffer `cur` over the z planes [z0, z1) (z1 < 0: all).
+cudaError_t launch_step_kernel(lbm_ctx* ctx, int cur, int kind, cudaStream_t s, long long* launches, int z0 = 0,
+                               int z1 = -1) {
   lbm::StepParams p;
   p.g = ctx->g;
   p.omega = ctx->omega;
   p.flag = ctx->d_flag;
   p.tab = ctx->tab;
-  cudaError_t e = cudaSuccess;
-  static_assert(kGraphSteps % 2 == 0, "a captured run must return to its starting state");
-  if (!ctx->aa) {
-    for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
-      if (ctx->zero_grad[face]) e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[cur], face, s);
-      else if (ctx->bounce[face]) e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[cur], face, 0, s);
-      else continue;
-      ++*launches;
-    }
-    if (e != cudaSuccess) return e;
-    p.src = ctx->buf[cur];
-    p.dst = ctx->buf[cur ^ 1];
-    lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepPingPong);
-    ++*launches;
-    return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, step_mode(ctx), lbm::kStepPingPong, p, s);
+  p.src = ctx->buf[ctx->aa ? 0 : cur];
+  p.dst = ctx->buf[ctx->aa ? 0 : cur ^ 1];
+  lbm::fill_slab_bases(&p, ctx->elem, kind);
+  if (z1 >= 0) {
+    p.z0 = z0;
+    p.z1 = z1;
   }
-  p.src = ctx->buf[0];
-  p.dst = ctx->buf[0];
-  if (layout == lbm::kLayoutAAPushed) {
-    lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepAAOwn);
-    ++*launches;
-    return lbm::launch_stream_collide(ctx->storage, 0, step_mode(ctx), lbm::kStepAAOwn, p, s);
-  }
-  for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
-    if (ctx->zero_grad[face]) e = lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[0], face, s);
-    else if (ctx->inflow[face])
-      e = lbm::launch_fill_inflow(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->feq_in_own[face], s);
-    else if (ctx->bounce[face])
-      e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 1, s);
-    else continue;
-    ++*launches;
-  }
-  if (e != cudaSuccess) return e;
-  lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepAANeighbour);
   ++*launches;
-  e = lbm::launch_stream_collide(ctx->storage, 0, step_mode(ctx), lbm::kStepAANeighbour, p, s);
+  return lbm::launch_stream_collide(ctx->storage, kind == lbm::kStepPingPong ? ctx->cfg.fp64_moments : 0,
+                                    step_mode(ctx), kind, p, s);
+}
+
+// After an AA neighbour step (interior sites only): what each x face returns into the fluid
+// sites' slots -- the ghosts' pushes (zero gradient, inflow) or the wall's reflections.
+cudaError_t post_step_returns(lbm_ctx* ctx, int kind, cudaStream_t s, long long* launches) {
+  if (kind != lbm::kStepAANeighbour) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
   for (int face = 0; face < 2 && e == cudaSuccess; ++face) {
     if (ctx->bounce[face])
       e = lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 2, s);
     else if (ctx->zero_grad[face] || ctx->inflow[face])
       e = lbm::launch_aa_ghost_push(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, ctx->zero_grad[face] ? 1 : 0,
                                     ctx->feq_in[face], s);
-    else continue;
+    else
+      continue;
     ++*launches;
   }
+  return e;
+}
+
+// Issues one step on stream s and adds its launches to *launches.  Ping-pong: ghost fills,
+// then the fused kernel from buffer `cur` into the other.  AA (buffer 0, in place): from the
+// own layout, ghost fills in that layout, the neighbour step, then what the faces return into
+// the interior (leaves the pushed layout); from the pushed layout, the own-site step.
+cudaError_t issue_step(lbm_ctx* ctx, int cur, int layout, cudaStream_t s, long long* launches) {
+  static_assert(kGraphSteps % 2 == 0, "a captured run must return to its starting state");
+  const int kind = step_kind(ctx, layout);
+  cudaError_t e = pre_step_fills(ctx, cur, kind, kFillAll, s, launches);
+  if (e == cudaSuccess) e = launch_step_kernel(ctx, cur, kind, s, launches);
+  if (e == cudaSuccess) e = post_step_returns(ctx, kind, s, launches);
   return e;
 }
 
@@ -565,7 +589,7 @@ cudaError_t init_slab(lbm_ctx* ctx, int k, bool fill_ghosts) {
   for (int sub = 0; sub < 2 && e == cudaSuccess; ++sub) {
     e = lbm::launch_init(ctx->storage, ctx->cfg.equilibrium, ctx->g, ctx->tab, ctx->buf[0], slot + sub * M,
                          slot + (2 + sub) * M, slot + (8 + sub) * M, sub * n + sl.z0 * nxy, sl.m, 2 * M, s,
-                         ctx->d_flag, 0);
+                         ctx->d_flag, ctx->aa ? 1 : 0);
     ++ctx->launches;
   }
   for (int face = 0; face < 2 && e == cudaSuccess && fill_ghosts; ++face) {
@@ -597,24 +621,6 @@ cudaError_t moments_out(lbm_ctx* ctx, int k, long long q, const void* buf, int l
   return e;
 }
 
-// One ping-pong step over the planes of slab k (buffer cur into cur ^ 1; ghosts already filled).
-cudaError_t slab_step(lbm_ctx* ctx, int k) {
-  const Slab sl = slab_at(ctx, k);
-  lbm::StepParams p;
-  p.g = ctx->g;
-  p.omega = ctx->omega;
-  p.flag = ctx->d_flag;
-  p.tab = ctx->tab;
-  p.src = ctx->buf[ctx->cur];
-  p.dst = ctx->buf[ctx->cur ^ 1];
-  lbm::fill_slab_bases(&p, ctx->elem, lbm::kStepPingPong);
-  p.z0 = sl.z0;
-  p.z1 = sl.z1;
-  ++ctx->launches;
-  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments, step_mode(ctx), lbm::kStepPingPong, p,
-                                    ctx->stream);
-}
-
 // The copy and init streams start after the work already queued on the context's stream ...
 cudaError_t fork_copies(lbm_ctx* ctx) {
   cudaError_t e = cudaEventRecord(ctx->mark, ctx->stream);
@@ -633,20 +639,26 @@ cudaError_t join_copies(lbm_ctx* ctx) {
   return e;
 }
 
-// lbm_advance_fields for pinned host fields and ping-pong streaming.  Slab by slab: the input
-// copy engine fills input slots, init runs on each slab as it lands, and the output copy
-// engine drains each slab's moments as soon as they are computed, so both directions of the
-// host link and the kernels overlap.  n == 0: moments follow init; n == 1: the step of a slab
-// follows the init of every slab within the pull reach of its planes; n >= 2: init for all
-// slabs, n - 1 whole-grid steps, then the last step slab by slab with its moments.
+// lbm_advance_fields for pinned host fields.  Slab by slab: the input copy engine fills input
+// slots, init runs on each slab as it lands (on its own stream), and the output copy engine drains
+// each slab's moments as soon as they are computed, so both directions of the host link and the
+// kernels overlap.  n == 0: moments follow init; n == 1: the step of a slab follows the init of
+// every slab within the pull reach of its planes; n >= 2: init for all slabs, n - 1 whole-grid
+// steps, then the last step slab by slab with its moments.  AA streaming: the neighbour step of
+// a slab reads and writes only slots of sites within its reach, each slot by one site, so slab
+// steps may run in any order once those sites are initialised; the moments of the pushed layout
+// read only what the slab's own sites pushed; what the x faces return into the fluid (for the
+// next step) follows all slab steps.
 lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double* const out[3]) {
   const int N = slab_count(ctx);
   ctx->cur = 0;
-  ctx->layout = lbm::kLayoutPlain;
+  ctx->layout = ctx->aa ? lbm::kLayoutAAOwn : lbm::kLayoutPlain;
   ctx->initialized = false;
   LBM_CK(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(unsigned int), ctx->stream));
-  lbm_status st = fill_inflow_faces(ctx);
+  lbm_status st = fill_inflow_faces(ctx);  // ping-pong: constant inflow ghosts of both buffers
   if (st != LBM_OK) return st;
+  const int kind1 = step_kind(ctx, ctx->layout);  // the first step's kind
+  if (n == 1) LBM_CK(ctx, pre_step_fills(ctx, 0, kind1, kFillInflow, ctx->stream, &ctx->launches));
   LBM_CK(ctx, fork_copies(ctx));
   for (int k = 0; k < N && k < kRing; ++k) LBM_CK(ctx, stage_in(ctx, k, in));
   // n == 1: need[k] = the last slab, in init order, holding a plane within kReach of slab k.  A
@@ -670,51 +682,49 @@ lbm_status advance_staged(lbm_ctx* ctx, double* const in[3], long long n, double
   std::stable_sort(fill_order.begin(), fill_order.end(), [&](int a, int b) { return need[a] < need[b]; });
   size_t next = 0, next_fill = 0;
   long long q = 0;
+  // where the moments of the state after a step of `kind` are read
+  auto after = [&](int kind) {
+    return kind == lbm::kStepPingPong ? lbm::kLayoutPlain
+                                      : kind == lbm::kStepAANeighbour ? lbm::kLayoutAAPushed : lbm::kLayoutAAOwn;
+  };
+  void* const out_buf = ctx->buf[ctx->aa ? 0 : 1];  // holds the state after one step from buffer 0
   for (int j = 0; j < N; ++j) {
     LBM_CK(ctx, init_slab(ctx, j, n == 1));
     if (j + kRing < N) LBM_CK(ctx, stage_in(ctx, j + kRing, in));
     // what follows needs init up to slab j (and no further): wait for in_free[j % kRing]
     if (n == 0) {
       LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
-      LBM_CK(ctx, moments_out(ctx, j, q++, ctx->buf[0], lbm::kLayoutPlain, out));
+      LBM_CK(ctx, moments_out(ctx, j, q++, ctx->buf[0], ctx->layout, out));
     } else if (n == 1 && ((next < order.size() && step_need[order[next]] <= j) ||
                           (walls && next_fill < fill_order.size() && need[fill_order[next_fill]] <= j))) {
       LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_free[j % kRing], 0));
       for (; walls && next_fill < fill_order.size() && need[fill_order[next_fill]] <= j; ++next_fill) {
         const Slab sl = slab_at(ctx, fill_order[next_fill]);
-        for (int face = 0; face < 2; ++face) {
-          if (!ctx->bounce[face]) continue;
-          LBM_CK(ctx, lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[0], face, 0, ctx->stream,
-                                              sl.z0, sl.z1));
-          ++ctx->launches;
-        }
+        LBM_CK(ctx, pre_step_fills(ctx, 0, kind1, kFillWalls, ctx->stream, &ctx->launches, sl.z0, sl.z1));
       }
       for (; next < order.size() && step_need[order[next]] <= j; ++next) {
-        LBM_CK(ctx, slab_step(ctx, order[next]));
-        LBM_CK(ctx, moments_out(ctx, order[next], q++, ctx->buf[1], lbm::kLayoutPlain, out));
+        const Slab sl = slab_at(ctx, order[next]);
+        LBM_CK(ctx, launch_step_kernel(ctx, 0, kind1, ctx->stream, &ctx->launches, sl.z0, sl.z1));
+        LBM_CK(ctx, moments_out(ctx, order[next], q++, out_buf, after(kind1), out));
       }
     }
   }
   ctx->initialized = true;
+  if (n == 1) LBM_CK(ctx, post_step_returns(ctx, kind1, ctx->stream, &ctx->launches));
   if (n >= 2) {
     LBM_CK(ctx, cudaEventRecord(ctx->mark, ctx->init_stream));
     LBM_CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->mark, 0));
     st = run_steps(ctx, n - 1);
     if (st != LBM_OK) return st;
-    for (int face = 0; face < 2; ++face) {
-      if (ctx->zero_grad[face])
-        LBM_CK(ctx, lbm::launch_fill_zero_gradient(ctx->storage, ctx->g, ctx->buf[ctx->cur], face, ctx->stream));
-      else if (ctx->bounce[face])
-        LBM_CK(ctx, lbm::launch_bounce_back(ctx->storage, ctx->g, ctx->tab, ctx->buf[ctx->cur], face, 0,
-                                            ctx->stream));
-      else
-        continue;
-      ++ctx->launches;
-    }
+    const int kind = step_kind(ctx, ctx->layout);
+    LBM_CK(ctx, pre_step_fills(ctx, ctx->cur, kind, kFillAll, ctx->stream, &ctx->launches));
+    void* const last_buf = ctx->buf[ctx->aa ? 0 : ctx->cur ^ 1];
     for (int k = 0; k < N; ++k) {
-      LBM_CK(ctx, slab_step(ctx, k));
-      LBM_CK(ctx, moments_out(ctx, k, q++, ctx->buf[ctx->cur ^ 1], lbm::kLayoutPlain, out));
+      const Slab sl = slab_at(ctx, k);
+      LBM_CK(ctx, launch_step_kernel(ctx, ctx->cur, kind, ctx->stream, &ctx->launches, sl.z0, sl.z1));
+      LBM_CK(ctx, moments_out(ctx, k, q++, last_buf, after(kind), out));
     }
+    LBM_CK(ctx, post_step_returns(ctx, kind, ctx->stream, &ctx->launches));
   }
   if (n >= 1) advance(ctx);
   LBM_CK(ctx, join_copies(ctx));
@@ -737,7 +747,7 @@ lbm_status lbm_advance_fields(lbm_ctx* ctx, const double* rho, const double* u, 
   if (!rho || !u || !theta || !rho_out || !u_out || !theta_out) return fail(ctx, LBM_EINVAL, "NULL field pointer");
   if (n < 0) return fail(ctx, LBM_EINVAL, "n must be >= 0");
   DeviceGuard dg(ctx->device);
-  bool pinned = !on_device && !ctx->aa;
+  bool pinned = !on_device;
   for (const void* f : {static_cast<const void*>(rho), static_cast<const void*>(u), static_cast<const void*>(theta),
                         static_cast<const void*>(rho_out), static_cast<const void*>(u_out),
                         static_cast<const void*>(theta_out)})

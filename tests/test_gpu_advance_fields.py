@@ -167,12 +167,16 @@ def test_staged_moments_match_device_moments(B):
     _equal(pin, [t.cpu().numpy() for t in dev])
 
 
-def test_aa_context_runs_the_calls_in_turn(B):
-    nx, ny, nz, faces = 32, 16, 12, ["zero_gradient", INFLOW]
+@pytest.mark.parametrize("grid", ["one_slab", "ragged_inflow", "thin"])
+def test_aa_streaming(B, grid):
+    """AA contexts pipeline too: neighbour steps per slab in the own layout, moments of the pushed
+    layout, the faces' returns after all slabs; n = 3 ends with an own-site step."""
+    nx, ny, nz, faces = GRIDS[grid]
+    faces = faces and ["zero_gradient", INFLOW]
     wl = W.smooth_random(nx, ny, nz, seed=2, faces=faces)
     fields = _fields(wl)
     cfg = B.make_config(nx, ny, nz, wl.paper_tau(), "f32", wl.faces, streaming="aa")
-    for n in (0, 1, 2):
+    for n in ((0, 1, 2, 3) if grid != "thin" else (1, 2)):
         ref, ref_after = _composed(B, cfg, fields, n, more=1)
         got, got_after = _fused(B, cfg, fields, n, more=1)
         _equal(got, ref)

@@ -98,17 +98,18 @@ def test_closed_box_conserves_on_device(B):
             assert abs(t[4] - t0[4]) <= 1e-12 * abs(t0[4])
 
 
+@pytest.mark.parametrize("streaming", ["pingpong", "aa"])
 @pytest.mark.parametrize("shape", [(64, 2048, 20), (32, 32768, 10)])
-def test_fused_call_with_walls(B, shape):
+def test_fused_call_with_walls(B, shape, streaming):
     """Several slabs (8 planes) and slabs one plane thick, walls on both x faces: the fused call
     equals the separate calls bitwise."""
     torch = pytest.importorskip("torch")
     nx, ny, nz = shape
     wl = W.smooth_random(nx, ny, nz, seed=nz, mach=0.3, faces=["bounce_back", "bounce_back"])
     fields = _fields(wl)
-    cfg = B.make_config(nx, ny, nz, wl.paper_tau(), "f32", wl.faces)
+    cfg = B.make_config(nx, ny, nz, wl.paper_tau(), "f32", wl.faces, streaming=streaming)
     S = wl.sites
-    for n in (1, 2):
+    for n in (1, 2, 3):
         ctx = B.lbm_create(cfg)
         try:
             B.lbm_init(ctx, *fields)
