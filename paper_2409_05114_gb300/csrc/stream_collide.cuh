@@ -534,12 +534,13 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
 // 4 for FP32/FP16/BF16 storage with FP32 moments (<= 128 registers, 16 warps per SM), 3 for
-// FP32 with FP64 moments and for the entropic alpha, and no bound for FP64 storage (its 81
-// doubles need ~250).
+// FP32 with FP64 moments (FP64-pipe bound), and no bound for FP64 storage (its 81 doubles need
+// ~250).  The entropic alpha spills at 4 blocks (its 2 x 81 local values do not fit L1 either
+// way) and still runs 7 % (FP32) and 9 % (FP16) faster than at 3: latency hiding decides it.
 template <class Store, bool kF64Mom, int kEq>
 constexpr int sc_min_blocks() {
   if constexpr (std::is_same_v<Store, double>) return 1;
-  else if constexpr (kF64Mom || kEq == kEqEntropicAlpha) return 3;
+  else if constexpr (kF64Mom) return 3;
   else return 4;
 }
 
