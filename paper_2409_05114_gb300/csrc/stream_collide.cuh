@@ -538,17 +538,33 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 // ~250).  The entropic alpha spills at 4 blocks (its 2 x 81 local values do not fit L1 either
 // way) and still runs 7 % (FP32) and 9 % (FP16) faster than at 3: latency hiding decides it.
 template <class Store, bool kF64Mom, int kEq>
-constexpr int sc_min_blocks() {
+RD3Q81_HD constexpr int sc_min_blocks_128() {
   if constexpr (std::is_same_v<Store, double>) return 1;
   else if constexpr (kF64Mom) return 3;
   else return 4;
 }
 
+// Threads per block of the fused kernel.  The issue-bound equilibria (exact entropic, exact
+// W(theta)) run 4-7 % faster in 256-thread blocks; the series equilibrium, whose FP32 form is
+// bandwidth-bound, and FP16 storage run 1-4 % faster in 128-thread blocks.  The register budget
+// per thread is the same either way (sc_min_blocks scales with the block).
+template <class Store, bool kF64Mom, int kEq>
+RD3Q81_HD constexpr int sc_block() {
+  return (kEq == kEqEntropic || kEq == kEqSeriesExactW) && !std::is_same_v<Store, double> ? 2 * kScBlock : kScBlock;
+}
+
+template <class Store, bool kF64Mom, int kEq>
+RD3Q81_HD constexpr int sc_min_blocks() {
+  constexpr int b = sc_min_blocks_128<Store, kF64Mom, kEq>() * kScBlock / sc_block<Store, kF64Mom, kEq>();
+  return b < 1 ? 1 : b;
+}
+
 template <class Store, bool kF64Mom, int kEq, int kKind = kStepPingPong>
-__global__ void __launch_bounds__(kScBlock, sc_min_blocks<Store, kF64Mom, kEq>())
+__global__ void __launch_bounds__(sc_block<Store, kF64Mom, kEq>(), sc_min_blocks<Store, kF64Mom, kEq>())
     stream_collide_kernel(const StepParams p) {
   const long long nxy = static_cast<long long>(p.g.nx) * p.g.ny;
-  const long long t = p.z0 * nxy + static_cast<long long>(blockIdx.x) * kScBlock + threadIdx.x;
+  constexpr int kBlock = sc_block<Store, kF64Mom, kEq>();
+  const long long t = p.z0 * nxy + static_cast<long long>(blockIdx.x) * kBlock + threadIdx.x;
   if (t >= p.z1 * nxy) return;
   if (blockIdx.y == 0)
     site_update_slabs<Store, kF64Mom, 0, kEq, kKind>(p, static_cast<int>(t));
@@ -560,7 +576,8 @@ template <class Store, bool kF64Mom, int kEq = kEqSeries, int kKind = kStepPingP
 cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
   const long long n = static_cast<long long>(p.g.nx) * p.g.ny * (p.z1 - p.z0);
   if (n <= 0) return cudaSuccess;
-  const dim3 grid(static_cast<unsigned>((n + kScBlock - 1) / kScBlock), 2);
+  constexpr int kBlock = sc_block<Store, kF64Mom, kEq>();
+  const dim3 grid(static_cast<unsigned>((n + kBlock - 1) / kBlock), 2);
   if constexpr (kEq == kEqEntropicAlpha) {
     // the alpha solve keeps 2 x 81 values per thread in local memory: all of L1 for it (set on
     // the direct launches; graphs are captured only after those)
@@ -571,7 +588,7 @@ cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
                                cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     if (e != cudaSuccess) return e;
   }
-  stream_collide_kernel<Store, kF64Mom, kEq, kKind><<<grid, kScBlock, 0, s>>>(p);
+  stream_collide_kernel<Store, kF64Mom, kEq, kKind><<<grid, kBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
 
