@@ -123,8 +123,10 @@ typedef struct {
   lbm_bc face[6];     /* -x, +x, -y, +y, -z, +z.  This version accepts non-periodic kinds
                          on the two x faces only; y and z must be periodic. */
   int storage;        /* lbm_storage */
-  int fp64_moments;   /* 1: moment sums and temperature recovery in FP64 for FP32/FP16/BF16
-                         storage (no effect for LBM_F64); 0: FP32 */
+  int fp64_moments;   /* 1: moment sums and temperature recovery to FP64 quality for FP32/FP16/
+                         BF16 storage (no effect for LBM_F64): FP32 storage by cascaded
+                         double-word (float + float, ~2^-48 relative) sums at FP32 rates, FP16/BF16
+                         storage in FP64; 0: FP32 */
   void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
                          creates its own stream (which synchronises with the legacy
                          default stream) */

@@ -88,8 +88,43 @@ struct Moments {
 // <f, c^2> = 3 theta0 + <w, d c^2> (the weights' own moments are 1, 0, 3 theta0).
 // FP32 sums of FP32 populations are also taken over the deviations f_i - w_i: the same
 // moments, summed from numbers ~10x smaller than f_i, hence ~10x smaller rounding.
+// FP32 storage with FP64-quality moments: cascaded sums (Sum2 and Dot2 of Ogita, Rump and
+// Oishi) of the 81 stored values.  The running sums stay floats; the rounding error of every
+// addition (TwoSum) and product (TwoProd) collects in a second float, which is as accurate as
+// summing in twice the working precision -- about 2^-48, against 2^-53 for FP64, at FP32 rates
+// (this GPU runs FP64 at 1/64 of them).  c^2 and c_a / 2 are exact floats.
+__device__ __forceinline__ Moments<Dw> site_moments_dw(const float* f) {
+  float pr = f[0], qr = 0.0f, pe = 0.0f, qe = 0.0f, px = 0.0f, qx = 0.0f, py = 0.0f, qy = 0.0f, pz = 0.0f,
+        qz = 0.0f;
+  // p + q += a (v.hi + v.lo), a exact
+  auto acc = [](float& p, float& q, float a, Dw v) {
+    const Dw h = two_prod(a, v.hi);
+    const Dw t = two_sum(p, h.hi);
+    p = t.hi;
+    q = __fadd_rn(q, __fadd_rn(t.lo, __fmaf_rn(a, v.lo, h.lo)));
+  };
+  static_for<kPairs>([&](auto Pc) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
+    constexpr float c2 = static_cast<float>(rd3q81::kShellC2[d.shell]);
+    const float fp = f[1 + 2 * P], fm = f[2 + 2 * P];
+    const Dw sum = two_sum(fp, fm), dif = two_sum(fp, -fm);
+    const Dw t = two_sum(pr, sum.hi);
+    pr = t.hi;
+    qr = __fadd_rn(qr, __fadd_rn(t.lo, sum.lo));
+    acc(pe, qe, c2, sum);
+    if constexpr (d.hx != 0) acc(px, qx, 0.5f * d.hx, dif);
+    if constexpr (d.hy != 0) acc(py, qy, 0.5f * d.hy, dif);
+    if constexpr (d.hz != 0) acc(pz, qz, 0.5f * d.hz, dif);
+  });
+  return Moments<Dw>{fast_two_sum(pr, qr), two_sum(px, qx), two_sum(py, qy), two_sum(pz, qz), fast_two_sum(pe, qe)};
+}
+
 template <class Store, bool kF64Mom>
 __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* f, const LatticeTables& tb) {
+  if constexpr (kF64Mom && std::is_same_v<Store, float>) {
+    return site_moments_dw(f);
+  } else {
   using C = Codec<Store>;
   using R = typename C::Real;
   using M = std::conditional_t<kF64Mom, double, R>;
@@ -124,6 +159,7 @@ __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* 
     E += M(3.0 * rd3q81::kTheta0);
   }
   return Moments<M>{rho, jx, jy, jz, E};
+  }
 }
 
 // ---- entropic alpha (Eq. (delH)) -------------------------------------------------------
@@ -329,12 +365,28 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
                                            unsigned int* flag, const LatticeTables& tb) {
   using C = Codec<Store>;
   using R = typename C::Real;
-  const M irho = M(1) / mo.rho;
-  const M mux = mo.jx * irho, muy = mo.jy * irho, muz = mo.jz * irho;
-  const M mtheta = (mo.E * irho - (mux * mux + muy * muy + muz * muz)) * M(1.0 / 3.0);
-
-  const R rh = R(mo.rho);
-  const R theta = R(mtheta);
+  R rh, theta, mux, muy, muz;
+  if constexpr (std::is_same_v<M, Dw>) {
+    // double-word recovery of u and theta (site_moments_dw), rounded once to FP32
+    const Dw inv = dw_recip(mo.rho);
+    const Dw ux = dw_mul(mo.jx, inv), uy = dw_mul(mo.jy, inv), uz = dw_mul(mo.jz, inv);
+    const Dw u2 = dw_add(dw_add(dw_mul(ux, ux), dw_mul(uy, uy)), dw_mul(uz, uz));
+    const Dw th3 = dw_add(dw_mul(mo.E, inv), Dw{-u2.hi, -u2.lo});
+    rh = dw_to_float(mo.rho);
+    theta = dw_to_float(dw_mul(th3, Dw{kThirdHi, kThirdLo}));
+    mux = dw_to_float(ux);
+    muy = dw_to_float(uy);
+    muz = dw_to_float(uz);
+  } else {
+    const M irho = M(1) / mo.rho;
+    const M dux = mo.jx * irho, duy = mo.jy * irho, duz = mo.jz * irho;
+    const M mtheta = (mo.E * irho - (dux * dux + duy * duy + duz * duz)) * M(1.0 / 3.0);
+    rh = R(mo.rho);
+    theta = R(mtheta);
+    mux = R(dux);
+    muy = R(duy);
+    muz = R(duz);
+  }
   if (!(rh > R(0) && theta > R(0) && rh < R(FLT_MAX) && theta < R(FLT_MAX))) atomicOr(flag, 1u);
   // ---- equilibrium: App. B series (kEqSeries) or the exact minimiser of Sec. III ---------
   [[maybe_unused]] EqScalars<R> e;
@@ -342,20 +394,20 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   [[maybe_unused]] R lam[5];         // entropic: multipliers (mu, zeta, gamma)
   if constexpr (kEq == kEqSeries) {
     const R eta = theta * R(1.0 / rd3q81::kTheta0) - R(1);
-    eq_scalars<R>(R(mux), R(muy), R(muz), theta, eta, tab_na<R>(tb), tab_nb<R>(tb), e);
+    eq_scalars<R>(mux, muy, muz, theta, eta, tab_na<R>(tb), tab_nb<R>(tb), e);
 #pragma unroll
     for (int s = 0; s < kShells; ++s)
       W[s] = rh * poly4(C::kOffset ? tab_p<R>(tb, s) : tab_wp<R>(tb, s), eta);
   } else if constexpr (kEq == kEqSeriesExactW) {
     R An, Bn;
     if (!exact_weights<R>(theta, tb, W, An, Bn)) atomicOr(flag, 1u);
-    eq_scalars_ab<R>(R(mux), R(muy), R(muz), theta, An, Bn, e);
+    eq_scalars_ab<R>(mux, muy, muz, theta, An, Bn, e);
 #pragma unroll
     for (int s = 0; s < kShells; ++s) W[s] *= C::kOffset ? rh : rh * tab_w<R>(tb, s);
   } else {
     constexpr bool kDbl = std::is_same_v<R, double>;
     const R T[5] = {rh, R(mo.jx), R(mo.jy), R(mo.jz), R(mo.E)};
-    if (!entropic_multipliers<R>(T, R(mux), R(muy), R(muz), theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam))
+    if (!entropic_multipliers<R>(T, mux, muy, muz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam))
       atomicOr(flag, 1u);
   }
 
@@ -533,14 +585,15 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 }
 
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
-// 4 for FP32/FP16/BF16 storage with FP32 moments (<= 128 registers, 16 warps per SM), 3 for
-// FP32 with FP64 moments (FP64-pipe bound), and no bound for FP64 storage (its 81 doubles need
-// ~250).  The entropic alpha spills at 4 blocks (its 2 x 81 local values do not fit L1 either
+// 4 for FP32/FP16/BF16 storage (<= 128 registers, 16 warps per SM; FP32 with FP64-quality
+// moments too: its double-word sums run at FP32 rates, 9 % faster than at 3 blocks), 3 for
+// FP16/BF16 with FP64 moments (FP64-pipe bound), and no bound for FP64 storage (its 81 doubles
+// need ~250).  The entropic alpha spills at 4 blocks (its 2 x 81 local values do not fit L1 either
 // way) and still runs 7 % (FP32) and 9 % (FP16) faster than at 3: latency hiding decides it.
 template <class Store, bool kF64Mom, int kEq>
 RD3Q81_HD constexpr int sc_min_blocks_128() {
   if constexpr (std::is_same_v<Store, double>) return 1;
-  else if constexpr (kF64Mom) return 3;
+  else if constexpr (kF64Mom && !std::is_same_v<Store, float>) return 3;
   else return 4;
 }
 
