@@ -183,6 +183,23 @@ def test_aa_streaming(B, grid):
         _equal(got_after, ref_after)
 
 
+@pytest.mark.parametrize("streaming", ["pingpong", "aa"])
+@pytest.mark.parametrize("dims,faces", [((1, 1, 1), None), ((5, 1, 3), None), ((1, 3, 2), None),
+                                        ((3, 2, 1), ["zero_gradient", "bounce_back"]),
+                                        ((1, 2, 5), ["bounce_back", INFLOW])])
+def test_tiny_and_degenerate_grids(B, dims, faces, streaming):
+    """One-site rows, planes and grids (every pull wraps onto the same few sites; slabs of one plane
+    whose pull reach spans the whole grid) and one-site-wide open channels."""
+    wl = W.smooth_random(*dims, seed=sum(dims), mach=0.2, eta=0.03, faces=faces)
+    fields = _fields(wl)
+    cfg = B.make_config(*dims, wl.paper_tau(), "f32", wl.faces, streaming=streaming)
+    for n in (0, 1, 2):
+        ref, ref_after = _composed(B, cfg, fields, n, more=1)
+        got, got_after = _fused(B, cfg, fields, n, more=1)
+        _equal(got, ref)
+        _equal(got_after, ref_after)
+
+
 def test_rejects_bad_arguments(B):
     cfg = B.make_config(8, 8, 8, 0.1, "f32")
     S = 2 * 8 * 8 * 8
