@@ -69,10 +69,48 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
   // The equilibrium is evaluated in the arithmetic the step kernel uses for this storage:
   // FP64 for FP64 populations, FP32 otherwise (offset storage directly as feq/w - 1).
   using R = typename Codec<S>::Real;
-  R feq[kQ];
+  auto put = [&](int i, R v) {
+    const int io = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
+    S* q = buf + off + (own_slots ? io : i) * g.dir_stride;  // AA keeps f_i in the slot of -c_i
+    if constexpr (Codec<S>::kOffset)
+      Codec<S>::store(q, v - R(1));
+    else
+      Codec<S>::store(q, v);
+  };
   if constexpr (kEq == 0) {
-    equilibrium_all<R, Codec<S>::kOffset>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]), R(theta[k]), tab, feq);
-  } else if constexpr (kEq == 2) {
+    // The series equilibrium of equilibrium_all, with each pair stored as soon as it is
+    // evaluated: no array of 81 values stays live, so more warps fit on an SM.
+    constexpr bool kOverW = Codec<S>::kOffset;
+    constexpr bool dbl = std::is_same_v<R, double>;
+    const R rr = R(rho[k]), th = R(theta[k]);
+    const R eta = th / R(tab.theta0) - R(1);
+    R na[5], nb[5];
+    for (int j = 0; j < 5; ++j) {
+      na[j] = dbl ? R(tab.na[j]) : R(tab.naf[j]);
+      nb[j] = dbl ? R(tab.nb[j]) : R(tab.nbf[j]);
+    }
+    EqScalars<R> e;
+    eq_scalars<R>(R(u[k]), R(u[us + k]), R(u[2 * us + k]), th, eta, na, nb, e);
+    R W[kShells];
+    for (int sh = 0; sh < kShells; ++sh) {
+      R c[5];
+      for (int j = 0; j < 5; ++j)
+        c[j] = kOverW ? (dbl ? R(tab.p[sh][j]) : R(tab.pf[sh][j])) : (dbl ? R(tab.wp[sh][j]) : R(tab.wpf[sh][j]));
+      W[sh] = rr * poly4(c, eta);
+    }
+    put(0, W[0] * (e.c0 + e.k0 * (R(0) - e.t3)));
+    static_for<kPairs>([&](auto Pc) {
+      constexpr int P = decltype(Pc)::value;
+      constexpr int sh = rd3q81::kDirs[1 + 2 * P].shell;
+      R ev, od;
+      eq_pair_parts<P, R>(e, ev, od);
+      put(1 + 2 * P, W[sh] * (ev + od));
+      put(2 + 2 * P, W[sh] * (ev - od));
+    });
+    return;
+  }
+  R feq[kQ];
+  if constexpr (kEq == 2) {
     if (!equilibrium_all<R, Codec<S>::kOffset, true>(R(rho[k]), R(u[k]), R(u[us + k]), R(u[2 * us + k]),
                                                      R(theta[k]), tab, feq))
       atomicOr(flag, 1u);
@@ -81,15 +119,7 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
                                             feq))
       atomicOr(flag, 1u);
   }
-  static_for<kQ>([&](auto Ic) {
-    constexpr int i = decltype(Ic)::value;
-    constexpr int io = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);
-    S* q = buf + off + (own_slots ? io : i) * g.dir_stride;  // AA keeps f_i in the slot of -c_i
-    if constexpr (Codec<S>::kOffset)
-      Codec<S>::store(q, feq[i] - R(1));
-    else
-      Codec<S>::store(q, feq[i]);
-  });
+  static_for<kQ>([&](auto Ic) { put(decltype(Ic)::value, feq[decltype(Ic)::value]); });
 }
 
 // Moments of the stored populations (Eq. (conslaws)), returned in FP64; for offset storage
