@@ -115,3 +115,41 @@ def test_null_context_calls_are_einval(B):
     assert lib.lbm_totals(None, None) == B.LBM_EINVAL
     assert lib.lbm_advance_fields(None, None, None, None, 1, None, None, None, 0) == B.LBM_EINVAL
     assert lib.lbm_last_error(None) is not None
+
+
+def test_bounce_back_faces_validated(B):
+    """The bounce-back wall (the Sod setup of Sec. IV A) is an x-face kind: accepted on either x
+    face, alone or beside zero-gradient or inflow, with ghost layers like the other open kinds;
+    rejected on y and z faces and when paired with a periodic x face."""
+    ok = [["bounce_back", "bounce_back"], ["bounce_back", "zero_gradient"],
+          [("eq_inflow", 1.0, 0.1, 0, 0, 0.8), "bounce_back"]]
+    periodic = B.lbm_footprint(_cfg(B, nx=64))
+    for faces in ok:
+        fp = B.lbm_footprint(_cfg(B, nx=64, faces=faces))
+        assert fp > periodic                                    # ghost layers padded into every row
+    for faces in (["bounce_back", "periodic"], ["periodic", "bounce_back"],
+                  ["periodic", "periodic", "bounce_back"], ["periodic"] * 5 + ["bounce_back"]):
+        with pytest.raises(B.LbmError) as ei:
+            B.lbm_footprint(_cfg(B, faces=faces))
+        assert ei.value.status == B.LBM_EINVAL
+
+
+def test_footprint_counts_the_staging_ring(B):
+    """lbm_footprint covers the populations plus the host-transfer staging ring: two rings of 3 slots
+    of 10 FP64 rows of a z slab (about 2^20 sites per sublattice, whole planes), so at 512^2 x 8
+    planes the ring adds ~503 MB beyond one buffer pair, and AA halves only the populations."""
+    pp = B.lbm_footprint(_cfg(B, nx=512, ny=512, nz=8))
+    aa = B.lbm_footprint(_cfg(B, nx=512, ny=512, nz=8, streaming="aa"))
+    pops = 2 * 81 * 512 * 512 * 8 * 4                          # one buffer, both sublattices, FP32
+    assert pp - aa >= pops                                      # AA drops one buffer
+    ring = 2 * 3 * 10 * (4 * 512 * 512) * 8                     # 4 planes of 512^2 per slab
+    assert pp >= 2 * pops + ring
+    assert pp < 2 * pops * 1.01 + ring + (200 << 20)
+
+
+def test_advance_fields_null_arguments_are_einval(B):
+    lib = B._lib
+    assert lib.lbm_advance_fields(None, None, None, None, 0, None, None, None, 1) == B.LBM_EINVAL
+    with pytest.raises(ValueError):
+        B.lbm_advance_fields(None, np.zeros(2), np.zeros(6), np.zeros(2), 1,
+                             np.zeros(2), np.zeros(6), np.zeros(2, dtype=np.float32))
