@@ -255,9 +255,9 @@ lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz
  *
  * A server keeps many cases (each an lbm_config with its own grid, tau, faces and storage)
  * resident on the current device and advances all of them together: every time step is
- * one persistent fused kernel over a packed index of all resident sites (plus one batched
- * zero-gradient fill if any resident case needs it), and runs of up to 16 steps are
- * replayed as CUDA graphs.  Requests are admitted in submission order whenever a slot is
+ * one persistent fused kernel per storage type present, over a packed index of those cases'
+ * sites (plus one batched zero-gradient fill if any resident case needs it), and runs of up
+ * to 16 steps are replayed as CUDA graphs.  Requests are admitted in submission order whenever a slot is
  * free and the sum of resident case footprints (2 population buffers each) stays within
  * the HBM budget; admission (host-to-device copy and initialisation) runs on its own
  * stream while the resident cases compute.  A case leaves after its step count, or early
