@@ -42,7 +42,8 @@ read against the paper line by line:
 Parity pins (tests/test_oracle_*.py): lattice identities in exact arithmetic, the paper's
 printed moment-error column, W~ against its closed-form generating function, equilibrium
 moments, uniform-state fixed points, conservation on periodic grids, cubic-symmetry
-equivariance, the closed-form sound speed and the exact Sod/Riemann solution; the entropic
+equivariance, the closed-form sound speed, the shear-wave viscosity nu = tau theta0 that fixes the
+relaxation rate beta of ``collide`` (Sec. II) and the exact Sod/Riemann solution; the entropic
 equilibrium's constraints, optimality conditions and small-velocity limit; Delta H against the
 definition of H in 50-digit arithmetic, the root's small-deviation limit alpha -> 2 + a3/(3 a2)
 and the discrete H theorem of whole steps; the exact W(theta) against the entropic equilibrium at
