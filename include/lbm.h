@@ -246,7 +246,9 @@ int lbm_velocities(int* h, double* w);
  * (4096 partial sums of 8192 sites each), which every device that loads the library holds
  * until exit; grids with 2*nx*ny*nz > 33,554,432 sites are rejected with LBM_EINVAL.  The
  * first call on a device, with that device current, looks up the array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls share the array,
+ * (cudaGetSymbolAddress), so make it before any stream capture; the address is kept for the
+ * life of the process, so a cudaDeviceReset by the application invalidates the entry point on
+ * that device.  All calls share the array,
  * which keeps the last call's contents; calls that overlap on the GPU (different streams)
  * race on it.  Returns LBM_EINVAL for bad arguments, LBM_ECUDA if a launch fails. */
 lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz, double* out5, void* cuda_stream);

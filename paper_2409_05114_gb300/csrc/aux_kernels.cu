@@ -123,10 +123,10 @@ __global__ void init_kernel(Geometry g, LatticeTables tab, S* buf, const double*
 }
 
 // Moments of the stored populations (Eq. (conslaws)), returned in FP64; for offset storage
-// as deviations from the weights' own moments (1, 0, 3 theta0).  FP64 populations are summed
-// in FP64.  FP32/FP16/BF16 values are summed shell by shell in FP32 (at most 12 values of
-// one magnitude class, exact to the storage's own precision), and the 11 shell sums are
-// combined in FP64: FP64-quality moments at a tenth of the FP64 operations.
+// as deviations from the weights' own moments (1, 0, 3 theta0).  Every storage type is summed
+// in FP64 (shell by shell, then the 11 shell sums): the stored values are exact in FP64, so
+// the result carries FP64 rounding only.  Used by the conservation totals (a diagnostic, off
+// the step) and by the FP64-storage read-back; the other read-backs use site_moments_dw.
 template <class S>
 __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTables& tab, const S* buf, int layout,
                                              int sub, long long t, double& rho, double& jx, double& jy,
@@ -145,28 +145,28 @@ __device__ __forceinline__ void site_moments(const Geometry& g, const LatticeTab
       fv[i] = Codec<S>::load(buf + pop_offset(g, tab, layout, sub, t, i));
     });
   }
-  R sr[kShells], sx[kShells], sy[kShells], sz[kShells];
+  double sr[kShells], sx[kShells], sy[kShells], sz[kShells];
 #pragma unroll
-  for (int s = 0; s < kShells; ++s) sr[s] = sx[s] = sy[s] = sz[s] = R(0);
+  for (int s = 0; s < kShells; ++s) sr[s] = sx[s] = sy[s] = sz[s] = 0.0;
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
-    const R f = fv[i];
+    const double f = static_cast<double>(fv[i]);
     sr[d.shell] += f;
-    if constexpr (d.hx != 0) sx[d.shell] += R(0.5 * d.hx) * f;
-    if constexpr (d.hy != 0) sy[d.shell] += R(0.5 * d.hy) * f;
-    if constexpr (d.hz != 0) sz[d.shell] += R(0.5 * d.hz) * f;
+    if constexpr (d.hx != 0) sx[d.shell] += 0.5 * d.hx * f;
+    if constexpr (d.hy != 0) sy[d.shell] += 0.5 * d.hy * f;
+    if constexpr (d.hz != 0) sz[d.shell] += 0.5 * d.hz * f;
   });
   rho = jx = jy = jz = e = 0.0;
   static_for<kShells>([&](auto Sc) {
     constexpr int s = decltype(Sc)::value;
     constexpr double c2 = rd3q81::kShellC2[s];
     const double ws = Codec<S>::kOffset ? tab.w[s] : 1.0;
-    rho += ws * static_cast<double>(sr[s]);
-    e += ws * c2 * static_cast<double>(sr[s]);
-    jx += ws * static_cast<double>(sx[s]);
-    jy += ws * static_cast<double>(sy[s]);
-    jz += ws * static_cast<double>(sz[s]);
+    rho += ws * sr[s];
+    e += ws * c2 * sr[s];
+    jx += ws * sx[s];
+    jy += ws * sy[s];
+    jz += ws * sz[s];
   });
   if constexpr (Codec<S>::kOffset) {
     rho += 1.0;

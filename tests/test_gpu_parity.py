@@ -158,8 +158,12 @@ def test_storage_precision_errors_hit(B, storage, bound):
 
 
 def test_conservation_on_device(B):
+    """Sum rho, rho u and <f, c^2> over a periodic grid are conserved by ten steps: FP64 to
+    round-off; FP32 storage to the rounding of the stored values (the step's f~eq-shaped
+    conservation projection removes the FP32 defects of each update).  lbm_totals sums the
+    stored values in FP64."""
     wl = W.smooth_random(20, 12, 10, seed=8, mach=0.5, eta=0.1)
-    for storage, tol in (("f64", 1e-13), ("f32", 2e-6)):
+    for storage, tol in (("f64", 1e-13), ("f32", 2e-7)):
         cfg = B.make_config(wl.nx, wl.ny, wl.nz, 0.05, storage)
         ctx = B.lbm_create(cfg)
         try:
@@ -172,6 +176,7 @@ def test_conservation_on_device(B):
             B.lbm_destroy(ctx)
         np.testing.assert_array_equal(t1, again)           # deterministic reduction
         scale = np.array([t0[0]] * 4 + [t0[4]])
+        print(storage, "drift / scale", (t1 - t0) / scale)
         assert np.all(np.abs(t1 - t0) <= tol * scale), (storage, t1 - t0)
         ref = O.totals(O.init(wl.rho, wl.u, wl.theta))
         assert np.all(np.abs(t0 - ref) <= max(tol, 1e-13) * scale)

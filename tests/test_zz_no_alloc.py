@@ -27,7 +27,10 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+_TORCH_TYPE = {"f64": "float64", "f32": "float32", "f16": "float16", "bf16": "bfloat16"}
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
 def test_noalloc_totals_match_lbm_totals(B, storage):
     import torch
     wl = W.smooth_random(24, 12, 10, seed=21, mach=0.4, eta=0.05)
@@ -41,13 +44,19 @@ def test_noalloc_totals_match_lbm_totals(B, storage):
         B.lbm_get_populations(ctx, f)
     finally:
         B.lbm_destroy(ctx)
-    # the caller's own buffers, in the storage type (FP32 values are exact in FP32)
-    fin = f if storage == "f64" else f.to(torch.float32)
+    # The caller's own buffer in the storage type.  lbm_get_populations decodes the stored
+    # values exactly into FP64, so converting back recovers them: FP32 values directly, offset
+    # types as d = f/w - 1 (round to nearest recovers the stored d).
+    dt = getattr(torch, _TORCH_TYPE[storage])
+    if storage in ("f16", "bf16"):
+        w = torch.tensor(B.lbm_velocities()[1], dtype=torch.float64, device="cuda")
+        fin = (f.view(2, 81, -1) / w.view(1, 81, 1) - 1.0).reshape(-1).to(dt)
+    else:
+        fin = f.to(dt)
     out = torch.empty(5, dtype=torch.float64, device="cuda")
     code = B.STORAGE[storage]
-    # the tolerance of the conservation tests: lbm_totals sums FP32 storage shell by shell
-    # in FP32, this entry point sums every value in FP64
-    tol = 1e-13 if storage == "f64" else 2e-6
+    # both sides sum the same stored values in FP64 (in different orders)
+    tol = 1e-13
     scale = np.array([ref[0]] * 4 + [ref[4]])
     for _ in range(2):
         out.fill_(float("nan"))
