@@ -146,7 +146,8 @@ def gpu_index_for_smi(local_rank: int) -> str:
     return str(local_rank)
 
 
-KERNEL_SOURCES = ("stream_collide.cuh", "device_common.cuh", "lbm_internal.h", "rd3q81.h", "sc_f32.cu")
+KERNEL_SOURCES = ("stream_collide.cuh", "stream_collide_pair.cuh", "device_common.cuh", "lbm_internal.h", "rd3q81.h",
+                  "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu")
 
 
 def kernel_source_sha() -> str:

@@ -1,5 +1,8 @@
 // Host-side construction of the lattice constants (FP64), from Table "tab:weights" and the
 // series temperature weights of App. B, Eq. (zeroveleqseries).
+#include <algorithm>
+#include <cstdlib>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -66,6 +69,16 @@ void build_lattice_tables(LatticeTables* t) {
   t->theta0f = static_cast<float>(t0);
   t->theta0x3_dw[0] = static_cast<float>(3.0 * t0);
   t->theta0x3_dw[1] = static_cast<float>(3.0 * t0 - static_cast<double>(t->theta0x3_dw[0]));
+  // k_s: the largest |h_a| over the shell's members (every nonzero component has it)
+  int kmax[kShells] = {};
+  for (int i = 1; i < kQ; ++i) {
+    const int a[3] = {kDirs[i].hx, kDirs[i].hy, kDirs[i].hz};
+    for (int c = 0; c < 3; ++c) kmax[kDirs[i].shell] = std::max(kmax[kDirs[i].shell], std::abs(a[c]));
+  }
+  for (int s = 0; s < kShells; ++s) {
+    t->wc2f[s] = static_cast<float>(w[s] * kShellC2[s]);
+    t->whkf[s] = static_cast<float>(w[s] * 0.5 * kmax[s]);
+  }
   for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
   for (int i = 0; i < kQ; ++i) {
     t->opp[i] = i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1);

@@ -41,6 +41,8 @@ struct LatticeTables {
   float naf[5], nbf[5];
   float theta0f;
   float theta0x3_dw[2];  // 3 theta0 as a double word hi + lo (moment read-back of offset storage)
+  float wc2f[kShells];   // w_s c_s^2 (moment sums of offset storage)
+  float whkf[kShells];   // w_s k_s / 2, k_s the nonzero |h_a| of shell s (momentum sums)
   double wdir[kQ];  // w_i per direction (decoding offset storage in the auxiliary kernels)
   // In-place (AA) streaming: opp[i] = index of -c_i; the site that pulls f_i from site n of
   // sublattice s is n - push_d[s][i][0..2] on sublattice push_d[s][i][3].
