@@ -257,7 +257,8 @@ lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz
  *
  * A server keeps many cases (each an lbm_config with its own grid, tau, faces and storage)
  * resident on the current device and advances all of them together: every time step is
- * one persistent fused kernel per storage type present, over a packed index of those cases'
+ * one persistent fused kernel per kind of case present (storage type and equilibrium), over a
+ * packed index of those cases'
  * sites (plus one batched zero-gradient fill if any resident case needs it), and runs of up
  * to 16 steps are replayed as CUDA graphs.  Requests are admitted in submission order whenever a slot is
  * free and the sum of resident case footprints (2 population buffers each) stays within
@@ -276,6 +277,8 @@ typedef struct {
   int resident_cases;
   size_t resident_bytes, peak_resident_bytes;
   double busy_seconds;              /* scheduler time spent running ticks */
+  double resident_byte_seconds;     /* resident bytes integrated over that time (per tick, the larger of
+                                       the counts before and after it): mean resident = this / busy */
 } lbm_server_stats;
 
 /* Creates a server on the current device.  hbm_budget_bytes bounds the resident cases'
@@ -283,7 +286,9 @@ typedef struct {
 lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server** out);
 
 /* Queues one case: configuration (storage FP32, FP16 or BF16 offsets, fp64_moments = 0,
- * the series equilibrium; cuda_stream is ignored), initial fields in host memory (layout as lbm_init; copied
+ * the series equilibrium of App. B or the exact entropic equilibrium of Sec. III, BGK collision,
+ * ping-pong streaming, x faces periodic, zero-gradient or equilibrium inflow; cuda_stream is
+ * ignored), initial fields in host memory (layout as lbm_init; copied
  * before the call returns) and nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case
  * alone exceeds the budget, LBM_EINVAL for an invalid configuration. */
 lbm_status lbm_submit(lbm_server* srv, const lbm_config* cfg, const double* rho, const double* u,

@@ -1,5 +1,6 @@
 // Continuous-batching server: many independent RD3Q81 cases resident on one GPU, advanced
-// together by one persistent fused kernel per time step.
+// together by one persistent fused kernel per time step and per kind of case (storage type and
+// equilibrium: the App. B series, or the exact entropic equilibrium of Sec. III, both with BGK).
 //
 // Each admitted case owns two population buffers (ping-pong) and a slot in a device case
 // table.  A step of the whole batch is (a) one batched zero-gradient ghost fill (only if a
@@ -39,6 +40,7 @@ struct CaseDesc {
   double omega;
   unsigned int* flag;
   int storage;         // kF32, kF16Off or kBF16Off
+  int eq;              // kEqSeries or kEqEntropic
   int parity;          // buffer holding the state at the start of the tick
   int tiles_sub;       // ceil(nx*ny*nz / kScBlock)
   int zg_face[2];      // zero-gradient at -x / +x
@@ -56,21 +58,21 @@ __device__ __forceinline__ int find_case(const long long* first, int ncases, lon
   return lo;
 }
 
-template <class S>
+template <class S, int kEq>
 __device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, int par, const LatticeTables& tab) {
   if (sub == 0)
-    site_update<S, false, 0>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
+    site_update<S, false, 0, kEq>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
   else
-    site_update<S, false, 1>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
+    site_update<S, false, 1, kEq>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
 }
 
-// Step k of the current tick for the resident cases of one storage type S (one kernel per type,
-// so each holds one storage's site update: a kernel with all three overflowed the instruction
-// cache).  Grid: persistent (SMs x resident blocks); block b handles tiles b, b + gridDim.x, ...
-// No block waits on another.
+// Step k of the current tick for the resident cases of one group (storage type S, equilibrium
+// kEq): one kernel per group, so each holds one site update (a kernel with several overflowed the
+// instruction cache).  Grid: persistent (SMs x resident blocks); block b handles tiles b,
+// b + gridDim.x, ...  No block waits on another.
 // Tiles [0, half) are the P sublattice of every case of the group, [half, 2 half) the R
 // sublattice: blocks working side by side then mostly run one of the two compiled site updates.
-template <class S>
+template <class S, int kEq>
 __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
                                                                long long half, int k, const LatticeTables tab) {
   __shared__ long long s_first[kMaxServerCases];
@@ -85,19 +87,38 @@ __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc
     const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
     if (t >= n) continue;
     const int par = (cd.parity + k) & 1;
-    served_site<S>(cd, sub, static_cast<int>(t), par, tab);
+    served_site<S, kEq>(cd, sub, static_cast<int>(t), par, tab);
   }
 }
 
-// Resident cases grouped by storage type: the case table lists the FP32 cases, then FP16, then
-// BF16; each group's tiles are numbered from 0 for its own kernel.
-constexpr int kStorageGroups = 3;
-constexpr int kGroupStorage[kStorageGroups] = {kF32, kF16Off, kBF16Off};
+// Resident cases grouped by kind (storage type, equilibrium): the case table lists the groups
+// in this order; each group's tiles are numbered from 0 for its own kernel.
+constexpr int kGroups = 6;
+constexpr int kGroupStorage[kGroups] = {kF32, kF16Off, kBF16Off, kF32, kF16Off, kBF16Off};
+constexpr int kGroupEq[kGroups] = {kEqSeries, kEqSeries, kEqSeries, kEqEntropic, kEqEntropic, kEqEntropic};
 struct TickPlan {
-  int first[kStorageGroups] = {0, 0, 0};    // first case of the group in the table
-  int count[kStorageGroups] = {0, 0, 0};
-  long long tiles[kStorageGroups] = {0, 0, 0};  // P-sublattice tiles of the group (the R half is as many)
+  int first[kGroups] = {};      // first case of the group in the table
+  int count[kGroups] = {};
+  long long tiles[kGroups] = {};  // P-sublattice tiles of the group (the R half is as many)
 };
+
+template <class S, int kEq>
+void launch_served(const CaseDesc* d, int count, long long tiles, int k, const LatticeTables& tab, int grid,
+                   cudaStream_t s) {
+  served_step_kernel<S, kEq><<<grid, kScBlock, 0, s>>>(d, count, tiles, k, tab);
+}
+
+void launch_group(int gi, const CaseDesc* d, int count, long long tiles, int k, const LatticeTables& tab, int grid,
+                  cudaStream_t s) {
+  switch (gi) {
+    case 0: launch_served<float, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
+    case 1: launch_served<__half, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
+    case 2: launch_served<__nv_bfloat16, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
+    case 3: launch_served<float, kEqEntropic>(d, count, tiles, k, tab, grid, s); break;
+    case 4: launch_served<__half, kEqEntropic>(d, count, tiles, k, tab, grid, s); break;
+    default: launch_served<__nv_bfloat16, kEqEntropic>(d, count, tiles, k, tab, grid, s);
+  }
+}
 
 template <class T>
 __device__ __forceinline__ void copy_edge(T* buf, const CaseDesc& cd, long long row, int face) {
@@ -252,15 +273,18 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
     for (int a = 0; a < 3; ++a)
       SRV_CK(s, cudaMemcpyAsync(su + a * cnt, r->in.data() + S + a * S + first, nb, cudaMemcpyHostToDevice, s->admit));
     SRV_CK(s, cudaMemcpyAsync(st, r->in.data() + 4 * S + first, nb, cudaMemcpyHostToDevice, s->admit));
-    SRV_CK(s, launch_init(r->cfg.storage, kEqSeries, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt, s->admit,
-                          s->d_flags + slot));
+    SRV_CK(s, launch_init(r->cfg.storage, r->cfg.equilibrium, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt,
+                          s->admit, s->d_flags + slot));
     ++s->stats.kernel_launches;
   }
   for (int face = 0; face < 2; ++face) {
     const lbm_bc& b = r->cfg.face[face];
     if (b.kind != LBM_BC_EQ_INFLOW) continue;
     Feq81 feq;
-    equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, s->tab, feq.v);
+    if (r->cfg.equilibrium == LBM_EQ_ENTROPIC)
+      entropic_all<double>(b.rho, b.ux, b.uy, b.uz, b.theta, s->tab, feq.v);
+    else
+      equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, s->tab, feq.v);
     for (int k = 0; k < 2; ++k) {
       SRV_CK(s, launch_fill_inflow(r->cfg.storage, res.g, s->tab, res.buf[k], face, feq, s->admit));
       ++s->stats.kernel_launches;
@@ -310,18 +334,10 @@ cudaGraphExec_t tick_graph(lbm_server* s, int ncases, const TickPlan& plan, long
       const int zb = static_cast<int>(std::min<long long>((total_rows + 255) / 256, 4096));
       served_zero_gradient_kernel<<<zb, 256, 0, cap>>>(s->d_cases, ncases, total_rows, k);
     }
-    for (int gi = 0; gi < kStorageGroups; ++gi) {
+    for (int gi = 0; gi < kGroups; ++gi) {
       if (plan.count[gi] == 0) continue;
       const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, 2 * plan.tiles[gi]));
-      const CaseDesc* d = s->d_cases + plan.first[gi];
-      switch (kGroupStorage[gi]) {
-        case kF32: served_step_kernel<float><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab); break;
-        case kF16Off:
-          served_step_kernel<__half><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab);
-          break;
-        default:
-          served_step_kernel<__nv_bfloat16><<<grid, kScBlock, 0, cap>>>(d, plan.count[gi], plan.tiles[gi], k, s->tab);
-      }
+      launch_group(gi, s->d_cases + plan.first[gi], plan.count[gi], plan.tiles[gi], k, s->tab, grid, cap);
     }
   }
   if (ok) ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
@@ -395,25 +411,28 @@ lbm_status run_tick(lbm_server* s) {
   const int ncases = static_cast<int>(s->active.size());
   long long total_rows = 0, min_left = s->active[0].steps_left;
   TickPlan plan;
-  std::vector<int> order;  // active cases grouped by storage type
-  for (int gi = 0; gi < kStorageGroups; ++gi) {
+  std::vector<int> order;  // active cases grouped by kind
+  for (int gi = 0; gi < kGroups; ++gi) {
     plan.first[gi] = static_cast<int>(order.size());
-    for (int c = 0; c < ncases; ++c)
-      if (s->active[c].req->cfg.storage == kGroupStorage[gi]) order.push_back(c);
+    for (int c = 0; c < ncases; ++c) {
+      const lbm_config& cf = s->active[c].req->cfg;
+      if (cf.storage == kGroupStorage[gi] && cf.equilibrium == kGroupEq[gi]) order.push_back(c);
+    }
     plan.count[gi] = static_cast<int>(order.size()) - plan.first[gi];
   }
-  if (static_cast<int>(order.size()) != ncases) return set_fatal(s, "a resident case has an unserved storage type");
+  if (static_cast<int>(order.size()) != ncases) return set_fatal(s, "a resident case has an unserved kind");
   for (int c = 0; c < ncases; ++c) {
     Resident& a = s->active[order[c]];
     CaseDesc& d = s->h_cases[c];
     int gi = 0;
-    while (gi + 1 < kStorageGroups && c >= plan.first[gi + 1]) ++gi;
+    while (gi + 1 < kGroups && c >= plan.first[gi + 1]) ++gi;
     d.g = a.g;
     d.buf[0] = a.buf[0];
     d.buf[1] = a.buf[1];
     d.omega = a.omega;
     d.flag = s->d_flags + a.slot;
     d.storage = a.req->cfg.storage;
+    d.eq = a.req->cfg.equilibrium;
     d.parity = a.parity;
     const long long n = static_cast<long long>(a.g.nx) * a.g.ny * a.g.nz;
     d.tiles_sub = static_cast<int>((n + kScBlock - 1) / kScBlock);
@@ -433,7 +452,7 @@ lbm_status run_tick(lbm_server* s) {
   SRV_CK(s, cudaGraphLaunch(g, s->compute));
   ++s->stats.graph_launches;
   int groups = 0;
-  for (int gi = 0; gi < kStorageGroups; ++gi) groups += plan.count[gi] > 0;
+  for (int gi = 0; gi < kGroups; ++gi) groups += plan.count[gi] > 0;
   s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + groups);
   ++s->stats.ticks;
   SRV_CK(s, cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(unsigned int) * s->max_cases, cudaMemcpyDeviceToHost,
@@ -475,10 +494,17 @@ void worker_main(lbm_server* s) {
     if (admit_some(s) != LBM_OK) break;
     if (s->active.empty() && s->joining.empty()) continue;
     const auto t0 = Clock::now();
+    size_t held = 0;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      held = s->resident_bytes;
+    }
     if (run_tick(s) != LBM_OK) break;
     const auto t1 = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
-    s->stats.busy_seconds += std::chrono::duration<double>(t1 - t0).count();
+    const double dt = std::chrono::duration<double>(t1 - t0).count();
+    s->stats.busy_seconds += dt;
+    s->stats.resident_byte_seconds += dt * static_cast<double>(std::max(held, s->resident_bytes));
     s->stats.resident_cases = static_cast<int>(s->active.size());
   }
 }
@@ -523,7 +549,7 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
   cudaMemset(s->d_flags, 0, sizeof(unsigned int) * max_cases);
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel<float>, kScBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel<float, kEqSeries>, kScBlock, 0);
   s->grid_blocks = std::max(1, sms * std::max(1, per_sm));
   s->worker = std::thread(worker_main, s);
   *out = s;
@@ -546,9 +572,12 @@ lbm_status lbm_submit(lbm_server* s, const lbm_config* cfg, const double* rho, c
     s->err = "served cases take periodic, zero-gradient or equilibrium-inflow faces";
     return LBM_EINVAL;
   }
-  if (cfg->storage == LBM_F64 || cfg->fp64_moments || cfg->equilibrium != LBM_EQ_SERIES) {
+  if (cfg->storage == LBM_F64 || cfg->fp64_moments ||
+      (cfg->equilibrium != LBM_EQ_SERIES && cfg->equilibrium != LBM_EQ_ENTROPIC) ||
+      cfg->collision != LBM_COLLISION_BGK || cfg->streaming != LBM_STREAM_PINGPONG) {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments and the series equilibrium";
+    s->err = "served cases use FP32, FP16 or BF16 storage with FP32 moments, the series or the exact entropic "
+             "equilibrium, BGK collision and ping-pong streaming";
     return LBM_EINVAL;
   }
   auto r = std::make_shared<Request>();

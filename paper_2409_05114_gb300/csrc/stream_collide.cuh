@@ -419,12 +419,14 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   // f_i <- f_i + omega D_i with D_i = f~eq_i - f_i.  In exact arithmetic D has zero mass,
   // momentum and energy.  In FP32 it does not quite (f~eq is evaluated at rho, u, theta
   // rounded to FP32), and the defect would accumulate step after step.  For FP32 storage
-  // the defects of D are therefore summed (D is small, so the sums are accurate) and removed
-  // by subtracting w_i (a + b.c_i + g c_i^2) with a, b, g fixed by the weights' moments
+  // the defects of D are therefore summed (D is small, so the sums are accurate) and removed,
+  // for the series equilibria, by subtracting w_i (a + b.c_i + g c_i^2) with a, b, g fixed by
+  // the weights' moments
   // <w,1> = 1, <w,c c> = theta0 I, <w,c^2> = 3 theta0, <w,c^4> = 15 theta0^2.  The
   // correction has the shape of an equilibrium perturbation, so it adds no non-equilibrium
-  // part (with omega near 2 such a part would hardly decay).  The result equals the plain
-  // update in exact arithmetic; in FP32 it conserves to the rounding of the defect sums.
+  // part (with omega near 2 such a part would hardly decay).  The entropic equilibria take a
+  // correction shaped like f~eq itself (below).  The result equals the plain update in exact
+  // arithmetic; in FP32 it conserves to the rounding of the defect sums.
   constexpr bool kProject = std::is_same_v<Store, float>;
   R om = R(omega);                   // alpha beta with alpha = 2
   if constexpr (kEq == kEqEntropicAlpha) om = R(0.5) * om * alpha;
@@ -472,11 +474,16 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
     relax_rest(entropic_shell_factor<0, C::kOffset>(lam, rh, tb));
     entropic_pair_values<R, C::kOffset>(lam, rh, tb, relax_pair);
   }
-  if constexpr (kProject && kEq == kEqEntropicAlpha) {
-    // With the entropic alpha the update of the smallest populations decides alpha, so their
-    // correction must be small relative to them: the defects are removed by subtracting
-    // omega feq_i (k . phi_i), k from <feq, phi phi^T> k = defects (the Newton's 5x5 matrix at
-    // the final multipliers).  In exact arithmetic the defects and k are zero.
+  if constexpr (kProject && (kEq == kEqEntropic || kEq == kEqEntropicAlpha)) {
+    // With the exact entropic equilibrium the correction must be small relative to every
+    // population, the smallest included: with the entropic alpha their update decides alpha, and
+    // at Mach 2 the upstream outer-shell equilibria are orders of magnitude below w_i, so a
+    // w_i-shaped correction of the Newton's residual (up to its tolerance, 1e-6, every step, with
+    // the same sign) builds a non-equilibrium part there that omega near 2 hardly damps (the FP32
+    // Mach-2 blob failed within 100 steps that way; FP16 storage, which has no projection, ran).
+    // The defects are removed by subtracting omega feq_i (k . phi_i), k from
+    // <feq, phi phi^T> k = defects (the Newton's 5x5 matrix at the final multipliers), which is
+    // the shape of a change of the multipliers.  In exact arithmetic the defects and k are zero.
     R J[15];
     entropic_moment_matrix<R>(lam, rh, tb, J);
     R k[5] = {d1, dx, dy, dz, dE};
@@ -532,7 +539,8 @@ __device__ __forceinline__ void site_store(const Geometry& g, void* dst_buf, int
 // Updates interior site t of sublattice SUB: reads `src`, writes `dst` (both whole
 // population buffers of geometry g), relaxation omega, instability flag `flag`.
 // kF64Mom: the moment sums and the temperature recovery run in FP64 whatever the storage.
-template <class Store, bool kF64Mom, int SUB>
+// kEq: the equilibrium and collision (Equilibrium).
+template <class Store, bool kF64Mom, int SUB, int kEq = kEqSeries>
 __device__ __forceinline__ void site_update(const Geometry& g, const void* src_buf, void* dst_buf, double omega,
                                             unsigned int* flag, const LatticeTables& tb, int t) {
   using C = Codec<Store>;
@@ -544,7 +552,7 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
     f[decltype(Ic)::value] = C::load(p);
   });
   const auto mo = site_moments<Store, kF64Mom>(f, tb);
-  site_relax<Store>(f, mo, omega, flag, tb);
+  site_relax<Store, typename decltype(mo)::value_type, kEq>(f, mo, omega, flag, tb);
   site_store<Store>(g, dst_buf, SUB, zs[4] + ys[4] + xs[4], f);
 }
 
