@@ -262,7 +262,9 @@ lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz
  * sites (plus one batched zero-gradient fill if any resident case needs it), and runs of up
  * to 16 steps are replayed as CUDA graphs.  Requests are admitted in submission order whenever a slot is
  * free and the sum of resident case footprints (2 population buffers each) stays within
- * the HBM budget; admission (host-to-device copy and initialisation) runs on its own
+ * the HBM budget; when the oldest waiting request does not fit the free budget, the first of
+ * the next 15 that fits goes ahead of it, but no request is passed over more than 8 times.
+ * Admission (host-to-device copy and initialisation) runs on its own
  * stream while the resident cases compute.  A case leaves after its step count, or early
  * when one of its sites becomes unstable.  Its result is bitwise the same whether it is
  * served alone or in any mix (sites are independent and every case runs the same kernel),

@@ -7,7 +7,7 @@
 // resident case has such a face) and (b) one persistent kernel whose blocks walk a packed
 // index of 128-site tiles over all cases: the tile's case is found by binary search over the
 // cases' first-tile offsets, and the site is updated by the same device function as the
-// single-case kernel's (site_update).  Sites are independent, so a case's result is bitwise
+// single-case kernel's (site_update_table, with the case's slab bases from a table).  Sites are independent, so a case's result is bitwise
 // the same served alone and in any mix.  K steps form one "tick", captured once per (membership, K) as a CUDA graph and
 // replayed.  A scheduler thread admits queued requests by HBM footprint on a separate
 // stream while the current tick runs, and retires finished or unstable cases after it.
@@ -33,6 +33,10 @@ namespace {
 constexpr int kMaxServerCases = 1024;
 constexpr int kTickSteps = 16;            // longest tick (steps between scheduler decisions)
 constexpr long long kXferChunk = 1LL << 21;  // sites per host transfer chunk
+// Admission is first fit in submission order over the oldest kAdmitLookahead waiting requests;
+// a request passed over kMaxBypass times holds back every later one until it is admitted.
+constexpr int kAdmitLookahead = 16;
+constexpr int kMaxBypass = 8;
 
 struct CaseDesc {
   Geometry g;
@@ -58,13 +62,13 @@ __device__ __forceinline__ int find_case(const long long* first, int ncases, lon
   return lo;
 }
 
-template <class S, int kEq>
-__device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, int par, const LatticeTables& tab) {
-  if (sub == 0)
-    site_update<S, false, 0, kEq>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
-  else
-    site_update<S, false, 1, kEq>(cd.g, cd.buf[par], cd.buf[par ^ 1], cd.omega, cd.flag, tab, t);
-}
+// Slab base addresses of one resident case for one parity of its buffers (source buf[par],
+// destination buf[par ^ 1]), per target sublattice and direction: the table fill_slab_bases
+// writes for a single-case step.
+struct CaseSlabs {
+  const void* src[2][kQ];
+  void* dst[2][kQ];
+};
 
 // Step k of the current tick for the resident cases of one group (storage type S, equilibrium
 // kEq): one kernel per group, so each holds one site update (a kernel with several overflowed the
@@ -72,22 +76,44 @@ __device__ __forceinline__ void served_site(const CaseDesc& cd, int sub, int t, 
 // b + gridDim.x, ...  No block waits on another.
 // Tiles [0, half) are the P sublattice of every case of the group, [half, 2 half) the R
 // sublattice: blocks working side by side then mostly run one of the two compiled site updates.
+// When a block's tile belongs to another (case, parity, sublattice) than its last one, the block
+// copies that case's 2 x 81 slab bases into shared memory; the site update then reads them
+// there, as the single-case kernel reads its kernel parameters.
 template <class S, int kEq>
-__global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases, int ncases,
+__global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases,
+                                                               const CaseSlabs* __restrict__ slabs, int ncases,
                                                                long long half, int k, const LatticeTables tab) {
   __shared__ long long s_first[kMaxServerCases];
+  __shared__ const void* s_src[kQ];
+  __shared__ void* s_dst[kQ];
   for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].tile0;
   __syncthreads();
+  int have = -1;  // (case, parity, sublattice) whose slab bases are in shared memory
   for (long long tile = blockIdx.x; tile < 2 * half; tile += gridDim.x) {
     const int sub = tile >= half ? 1 : 0;
     const long long ptile = tile - sub * half;
     const int c = find_case(s_first, ncases, ptile);
     const CaseDesc& cd = cases[c];
+    const int par = (cd.parity + k) & 1;
+    const int key = (2 * c + par) * 2 + sub;
+    if (key != have) {  // the same for every thread of the block
+      __syncthreads();
+      const CaseSlabs& tb = slabs[2 * c + par];
+      for (int i = threadIdx.x; i < kQ; i += blockDim.x) {
+        s_src[i] = tb.src[sub][i];
+        s_dst[i] = tb.dst[sub][i];
+      }
+      __syncthreads();
+      have = key;
+    }
     const long long t = (ptile - cd.tile0) * kScBlock + threadIdx.x;
     const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
     if (t >= n) continue;
-    const int par = (cd.parity + k) & 1;
-    served_site<S, kEq>(cd, sub, static_cast<int>(t), par, tab);
+    const SharedSlabs sl{s_src, s_dst};
+    if (sub == 0)
+      site_update_table<S, false, 0, kEq, kStepPingPong>(cd.g, cd.omega, cd.flag, tab, sl, static_cast<int>(t));
+    else
+      site_update_table<S, false, 1, kEq, kStepPingPong>(cd.g, cd.omega, cd.flag, tab, sl, static_cast<int>(t));
   }
 }
 
@@ -103,20 +129,20 @@ struct TickPlan {
 };
 
 template <class S, int kEq>
-void launch_served(const CaseDesc* d, int count, long long tiles, int k, const LatticeTables& tab, int grid,
-                   cudaStream_t s) {
-  served_step_kernel<S, kEq><<<grid, kScBlock, 0, s>>>(d, count, tiles, k, tab);
+void launch_served(const CaseDesc* d, const CaseSlabs* sl, int count, long long tiles, int k, const LatticeTables& tab,
+                   int grid, cudaStream_t s) {
+  served_step_kernel<S, kEq><<<grid, kScBlock, 0, s>>>(d, sl, count, tiles, k, tab);
 }
 
-void launch_group(int gi, const CaseDesc* d, int count, long long tiles, int k, const LatticeTables& tab, int grid,
-                  cudaStream_t s) {
+void launch_group(int gi, const CaseDesc* d, const CaseSlabs* sl, int count, long long tiles, int k,
+                  const LatticeTables& tab, int grid, cudaStream_t s) {
   switch (gi) {
-    case 0: launch_served<float, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
-    case 1: launch_served<__half, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
-    case 2: launch_served<__nv_bfloat16, kEqSeries>(d, count, tiles, k, tab, grid, s); break;
-    case 3: launch_served<float, kEqEntropic>(d, count, tiles, k, tab, grid, s); break;
-    case 4: launch_served<__half, kEqEntropic>(d, count, tiles, k, tab, grid, s); break;
-    default: launch_served<__nv_bfloat16, kEqEntropic>(d, count, tiles, k, tab, grid, s);
+    case 0: launch_served<float, kEqSeries>(d, sl, count, tiles, k, tab, grid, s); break;
+    case 1: launch_served<__half, kEqSeries>(d, sl, count, tiles, k, tab, grid, s); break;
+    case 2: launch_served<__nv_bfloat16, kEqSeries>(d, sl, count, tiles, k, tab, grid, s); break;
+    case 3: launch_served<float, kEqEntropic>(d, sl, count, tiles, k, tab, grid, s); break;
+    case 4: launch_served<__half, kEqEntropic>(d, sl, count, tiles, k, tab, grid, s); break;
+    default: launch_served<__nv_bfloat16, kEqEntropic>(d, sl, count, tiles, k, tab, grid, s);
   }
 }
 
@@ -175,6 +201,7 @@ struct Request {
   Clock::time_point t_submit, t_done;
   lbm_status status = LBM_EBUSY;
   bool done = false;
+  int bypassed = 0;         // later requests admitted before this one
 };
 
 struct Resident {
@@ -203,6 +230,9 @@ struct lbm_server {
   cudaStream_t compute = nullptr, admit = nullptr;
   lbm::CaseDesc* d_cases = nullptr;
   lbm::CaseDesc* h_cases = nullptr;  // pinned staging
+  lbm::CaseSlabs* d_slabs = nullptr;  // per table position and parity (2 per case)
+  lbm::CaseSlabs* h_slabs = nullptr;  // pinned staging
+  long long slabs_version = -1;       // membership version the device table was written for
   unsigned int* d_flags = nullptr;
   unsigned int* h_flags = nullptr;   // pinned
   double* d_admit_scratch = nullptr;
@@ -298,7 +328,9 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
   return LBM_OK;
 }
 
-// Admits queued requests in FIFO order while a slot and budget are free.
+// Admits queued requests while a slot is free: the first of the oldest kAdmitLookahead that fits
+// the remaining budget, so that one large request at the head does not leave the budget idle;
+// a request passed over kMaxBypass times is admitted before any later one.
 lbm_status admit_some(lbm_server* s) {
   for (;;) {
     std::shared_ptr<Request> r;
@@ -306,9 +338,19 @@ lbm_status admit_some(lbm_server* s) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (s->queue.empty() || s->free_slots.empty()) return LBM_OK;
-      if (s->resident_bytes + s->queue.front()->footprint > s->budget) return LBM_OK;
-      r = s->queue.front();
-      s->queue.pop_front();
+      const int look = static_cast<int>(std::min<size_t>(s->queue.size(), kAdmitLookahead));
+      int pick = -1;
+      for (int q = 0; q < look; ++q) {
+        if (s->resident_bytes + s->queue[q]->footprint <= s->budget) {
+          pick = q;
+          break;
+        }
+        if (s->queue[q]->bypassed >= kMaxBypass) break;
+      }
+      if (pick < 0) return LBM_OK;
+      for (int q = 0; q < pick; ++q) ++s->queue[q]->bypassed;
+      r = s->queue[pick];
+      s->queue.erase(s->queue.begin() + pick);
       slot = s->free_slots.back();
       s->free_slots.pop_back();
       s->resident_bytes += r->footprint;
@@ -337,7 +379,8 @@ cudaGraphExec_t tick_graph(lbm_server* s, int ncases, const TickPlan& plan, long
     for (int gi = 0; gi < kGroups; ++gi) {
       if (plan.count[gi] == 0) continue;
       const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, 2 * plan.tiles[gi]));
-      launch_group(gi, s->d_cases + plan.first[gi], plan.count[gi], plan.tiles[gi], k, s->tab, grid, cap);
+      launch_group(gi, s->d_cases + plan.first[gi], s->d_slabs + 2 * plan.first[gi], plan.count[gi], plan.tiles[gi], k,
+                   s->tab, grid, cap);
     }
   }
   if (ok) ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess;
@@ -447,6 +490,25 @@ lbm_status run_tick(lbm_server* s) {
   }
   const int K = static_cast<int>(std::min<long long>(kTickSteps, min_left));
   SRV_CK(s, cudaMemcpyAsync(s->d_cases, s->h_cases, sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice, s->compute));
+  if (s->slabs_version != s->version) {
+    // table positions change only with membership; parity selects the table's half
+    for (int c = 0; c < ncases; ++c) {
+      const Resident& a = s->active[order[c]];
+      for (int par = 0; par < 2; ++par) {
+        StepParams sp{};
+        sp.src = a.buf[par];
+        sp.dst = a.buf[par ^ 1];
+        sp.g = a.g;
+        fill_slab_bases(&sp, storage_bytes(a.req->cfg.storage));
+        CaseSlabs& t = s->h_slabs[2 * c + par];
+        std::memcpy(t.src, sp.src_slab, sizeof(t.src));
+        std::memcpy(t.dst, sp.dst_slab, sizeof(t.dst));
+      }
+    }
+    SRV_CK(s, cudaMemcpyAsync(s->d_slabs, s->h_slabs, sizeof(CaseSlabs) * 2 * ncases, cudaMemcpyHostToDevice,
+                              s->compute));
+    s->slabs_version = s->version;
+  }
   cudaGraphExec_t g = tick_graph(s, ncases, plan, total_rows, K);
   if (!g) return set_fatal(s, "CUDA graph capture of a serving tick failed");
   SRV_CK(s, cudaGraphLaunch(g, s->compute));
@@ -539,6 +601,8 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
     return bail("stream creation failed");
   if (cudaMalloc(&s->d_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
       cudaMallocHost(&s->h_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
+      cudaMalloc(&s->d_slabs, sizeof(CaseSlabs) * 2 * max_cases) != cudaSuccess ||
+      cudaMallocHost(&s->h_slabs, sizeof(CaseSlabs) * 2 * max_cases) != cudaSuccess ||
       cudaMalloc(&s->d_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
       cudaMallocHost(&s->h_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
       cudaMalloc(&s->d_admit_scratch, 5 * kXferChunk * sizeof(double)) != cudaSuccess ||
@@ -680,6 +744,8 @@ lbm_status lbm_server_destroy(lbm_server* s) {
   drop_graphs(s);
   if (s->d_cases) cudaFree(s->d_cases);
   if (s->h_cases) cudaFreeHost(s->h_cases);
+  if (s->d_slabs) cudaFree(s->d_slabs);
+  if (s->h_slabs) cudaFreeHost(s->h_slabs);
   if (s->d_flags) cudaFree(s->d_flags);
   if (s->h_flags) cudaFreeHost(s->h_flags);
   if (s->d_admit_scratch) cudaFree(s->d_admit_scratch);

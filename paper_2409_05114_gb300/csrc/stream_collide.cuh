@@ -556,19 +556,37 @@ __device__ __forceinline__ void site_update(const Geometry& g, const void* src_b
   site_store<Store>(g, dst_buf, SUB, zs[4] + ys[4] + xs[4], f);
 }
 
+// Where a step finds the base address of each direction slab it reads and writes, per target
+// sublattice SUB and direction i (a compile-time constant in the unrolled loops):
+//   ParamSlabs   the kernel parameters (StepParams, filled by fill_slab_bases), for one case;
+//   SharedSlabs  a block's shared-memory copy of one served case's table (the same values).
+template <int SUB>
+struct ParamSlabs {
+  const StepParams& p;
+  __device__ __forceinline__ const void* src(int i) const { return p.src_slab[SUB][i]; }
+  __device__ __forceinline__ void* dst(int i) const { return p.dst_slab[SUB][i]; }
+};
+struct SharedSlabs {
+  const void* const* s;
+  void* const* d;
+  __device__ __forceinline__ const void* src(int i) const { return s[i]; }
+  __device__ __forceinline__ void* dst(int i) const { return d[i]; }
+};
+
 // The single-case form of site_update: the same phases, with the slab base addresses taken
-// from the kernel parameters instead of being computed per access.  kKind (StepKind) picks
-// where population i is read and written; the slab bases (fill_slab_bases) pick the
-// sublattice and slot:
+// from a table (Slabs) instead of being computed per access.  kKind (StepKind) picks where
+// population i is read and written; the slab bases (fill_slab_bases) pick the sublattice and
+// slot:
 //   ping-pong:    read the source of c_i (pull),  write own site;
 //   AA neighbour: read the source of c_i (pull),  write the site that pulls c_i next (push);
 //   AA own:       read own site,                  write own site.
-template <class Store, bool kF64Mom, int SUB, int kEq, int kKind = kStepPingPong>
-__device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
+template <class Store, bool kF64Mom, int SUB, int kEq, int kKind, class Slabs>
+__device__ __forceinline__ void site_update_table(const Geometry& g, double omega, unsigned int* flag,
+                                                  const LatticeTables& tab, const Slabs& sl, int t) {
   using C = Codec<Store>;
   using R = typename C::Real;
   int xs[9], ys[9], zs[9];
-  site_coords(p.g, t, xs, ys, zs);
+  site_coords(g, t, xs, ys, zs);
   R f[kQ];
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
@@ -577,10 +595,10 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
     constexpr int dx = kPull ? rd3q81::pull_disp(d.hx, SUB) : 0;
     constexpr int dy = kPull ? rd3q81::pull_disp(d.hy, SUB) : 0;
     constexpr int dz = kPull ? rd3q81::pull_disp(d.hz, SUB) : 0;
-    f[i] = C::load(static_cast<const Store*>(p.src_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
+    f[i] = C::load(static_cast<const Store*>(sl.src(i)) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]));
   });
-  const auto mo = site_moments<Store, kF64Mom>(f, p.tab);
-  site_relax<Store, typename decltype(mo)::value_type, kEq>(f, mo, p.omega, p.flag, p.tab);
+  const auto mo = site_moments<Store, kF64Mom>(f, tab);
+  site_relax<Store, typename decltype(mo)::value_type, kEq>(f, mo, omega, flag, tab);
   static_for<kQ>([&](auto Ic) {
     constexpr int i = decltype(Ic)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[i];
@@ -588,8 +606,13 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
     constexpr int dx = kPush ? rd3q81::pull_disp(-d.hx, SUB) : 0;
     constexpr int dy = kPush ? rd3q81::pull_disp(-d.hy, SUB) : 0;
     constexpr int dz = kPush ? rd3q81::pull_disp(-d.hz, SUB) : 0;
-    C::store(static_cast<Store*>(p.dst_slab[SUB][i]) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]), f[i]);
+    C::store(static_cast<Store*>(sl.dst(i)) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]), f[i]);
   });
+}
+
+template <class Store, bool kF64Mom, int SUB, int kEq, int kKind = kStepPingPong>
+__device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
+  site_update_table<Store, kF64Mom, SUB, kEq, kKind>(p.g, p.omega, p.flag, p.tab, ParamSlabs<SUB>{p}, t);
 }
 
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):

@@ -202,49 +202,60 @@ class ServedRequest:
     nsteps: int
     arrival_s: float
     tau: float           # the paper's tau passed to the library
+    equilibrium: str = "entropic"
+    family: str = ""
 
 
-def served_mix(n_requests: int = 12, seed: int = 5114, mean_interarrival_s: float = 0.1,
+def tgv_served_tau(n: int, mach: float, reynolds: float = 400.0, tau_min: float = 0.05) -> float:
+    """Paper tau of a served Taylor-Green case: the viscosity nu = tau theta0 (Sec. II) that gives
+    Re = U0 L / nu with L = n / (2 pi) (the field's length scale) and U0 = mach c_s, at the
+    Reynolds number of the paper's Mach-1 run (Sec. IV C: Re 400), but no lower than tau_min
+    (tau_lb 0.55)."""
+    u0 = mach * CS
+    return max(tau_min, u0 * (n / (2.0 * np.pi)) / (reynolds * THETA0))
+
+
+def served_mix(n_requests: int = 128, seed: int = 5114, mean_interarrival_s: float = 0.03,
                max_steps: int = 2000) -> list:
-    """Mixed-size request stream (seeded): Poisson arrivals; each request drawn uniformly from
-      * shock tubes nx x 4 x 4, nx in {256, 512, 1024, 2048}: rho 1 | 0.5, theta theta0 |
-        0.9 theta0, zero-gradient x faces, tau_lb 0.6;
-      * Taylor-Green n^3, n in {32, 48, 64, 96, 128, 160, 192}, Ma in {0.3, 0.5, 0.7}, tau_lb 0.55;
-      * blob flows 256x256x4, 512x128x4, 1024x256x4 at Ma 0.5 (inflow/outflow);
-    each with 200 .. max_steps steps and FP32 or FP16-offset storage.  The ranges are those in
-    which the series equilibrium with BGK runs the full 2000 steps: the strong Sod jump
-    (rho 1 | 0.125, theta 1 | 0.8; unstable at every tau tried once the shock meets the
-    outflow face), TGV
-    at Ma 1.0 (any tau tried), TGV at Ma 0.7 with tau_lb 0.51 and the Mach-2 blob leave it
-    within 20-300 steps and would be retired as unstable.  Field generation is cached per
-    shape."""
+    """Mixed-size request stream (seeded; the served-batch workload): Poisson arrivals, each
+    request drawn uniformly from three families:
+      * Sod-type shock tubes nx x 4 x 4, nx in {256, 512, 1024, 2048}: rho 1 | 0.125, theta
+        theta0 | 0.8 theta0, zero-gradient x faces, tau_lb 0.6 (the shock-tube workload);
+      * Taylor-Green vortices n^3, n in {32, 48, 64, 96, 128, 160, 192}, Ma in {0.3, 0.5, 0.7,
+        1.0}, tau from tgv_served_tau (Re 400, at least tau_lb 0.55);
+      * Mach-2 blob flows (blob, isentropic vortex, inflow / outflow) on 256x256x4, 512x128x4,
+        512x256x4 and 1024x256x4, tau_lb 0.55 (the Mach-2 workload);
+    each with 200 .. max_steps steps, FP32 or FP16-offset storage (even odds) and the exact
+    entropic equilibrium of Sec. III, with which every member of these families runs its 2000
+    steps (the series equilibrium fails on the Mach-2 blobs at once, on Mach-1 vortices and on
+    the strong Sod tube within a few hundred steps).  Field generation is cached per shape."""
     rng = np.random.default_rng(seed)
     cache = {}
     out = []
     t = 0.0
     for _ in range(n_requests):
         t += rng.exponential(mean_interarrival_s)
-        fam = rng.integers(0, 3)
+        fam = int(rng.integers(0, 3))
         if fam == 0:
             nx = int(rng.choice([256, 512, 1024, 2048]))
             key = ("tube", nx)
             if key not in cache:
-                cache[key] = shock_tube(nx=nx, rho_right=0.5, theta_right=0.9)
-            wl, tau = cache[key], paper_tau(0.6, "lb")
+                cache[key] = sod(nx=nx)
+            wl, tau, name = cache[key], paper_tau(0.6, "lb"), "shock_tube"
         elif fam == 1:
             n = int(rng.choice([32, 48, 64, 96, 128, 160, 192]))
-            ma = float(rng.choice([0.3, 0.5, 0.7]))
+            ma = float(rng.choice([0.3, 0.5, 0.7, 1.0]))
             key = ("tgv", n, ma)
             if key not in cache:
-                cache[key] = taylor_green(n, mach=ma, tau_lb=0.55)
-            wl, tau = cache[key], paper_tau(0.55, "lb")
+                cache[key] = taylor_green(n, mach=ma)
+            wl, tau, name = cache[key], tgv_served_tau(n, ma), "taylor_green"
         else:
-            shape = [(256, 256, 4), (512, 128, 4), (1024, 256, 4)][rng.integers(0, 3)]
+            shape = [(256, 256, 4), (512, 128, 4), (512, 256, 4), (1024, 256, 4)][int(rng.integers(0, 4))]
             key = ("blob",) + shape
             if key not in cache:
-                cache[key] = mach2_blob(*shape, mach=0.5, vortex=0.1)
-            wl, tau = cache[key], paper_tau(0.55, "literal")
+                cache[key] = mach2_blob(*shape)
+            wl, tau, name = cache[key], paper_tau(0.55, "lb"), "mach2_blob"
         steps = int(rng.integers(200, max_steps + 1))
         storage = "f32" if rng.random() < 0.5 else "f16"
-        out.append(ServedRequest(wl, storage, steps, t, tau))
+        out.append(ServedRequest(wl, storage, steps, t, tau, "entropic", name))
     return out

@@ -60,10 +60,13 @@ def _same(a, b, storage):
             assert float(np.max(np.abs(p - q))) <= _TOL[storage] * scale
 
 
+# Odd nx: ping-pong then runs the one-site-per-thread kernel whose arithmetic the AA kernels
+# share (with nx even, FP16/BF16 ping-pong runs the two-sites-per-thread kernel, which rounds
+# differently and is compared with the oracle in test_gpu_pair.py).
 CASES = [
-    ("tgv", lambda: W.taylor_green(12, mach=0.5), "lb"),
-    ("sod", lambda: W.sod(nx=64, ny=4, nz=3), "lb"),
-    ("blob", lambda: W.mach2_blob(40, 8, 4, mach=0.5, vortex=0.1), "literal"),
+    ("tgv", lambda: W.taylor_green(13, mach=0.5), "lb"),
+    ("sod", lambda: W.sod(nx=63, ny=4, nz=3), "lb"),
+    ("blob", lambda: W.mach2_blob(39, 8, 4, mach=0.5, vortex=0.1), "literal"),
 ]
 
 

@@ -1,6 +1,8 @@
 """Continuous-batching server (lbm_server_*): each case's result is bitwise the same served
-alone and in a mix (one kernel, independent sites) and agrees with the single-case API
-within the storage precision's tolerance; served results match the FP64 oracle,
+alone and in a mix (one kernel per kind of case, independent sites) and agrees with the
+single-case API within the storage precision's tolerance, for the series and the exact entropic
+equilibrium (a Mach-2 blob, a strong Sod tube and a Mach-1 Taylor-Green vortex among them);
+served results match the FP64 oracle,
 admission respects the HBM budget, an unstable case is retired early without disturbing
 the others, and waits are bounded.  Failures are made on the host (a state outside the
 equilibrium's range, an over-budget request, a short timeout); nothing faults the GPU."""
@@ -28,8 +30,8 @@ def _fields(wl):
             np.ascontiguousarray(wl.theta, dtype=np.float64).reshape(-1))
 
 
-def _single(B, wl, storage, tau, nsteps):
-    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces)
+def _single(B, wl, storage, tau, nsteps, eq="series"):
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, equilibrium=eq)
     ctx = B.lbm_create(cfg)
     try:
         B.lbm_init(ctx, *_fields(wl))
@@ -47,14 +49,18 @@ def _single(B, wl, storage, tau, nsteps):
 
 
 def _serve(B, items, budget=8 << 30, max_cases=16, timeout=300.0):
+    """items: (workload, storage, tau, steps[, equilibrium])."""
     srv = B.lbm_server_create(budget, max_cases)
     try:
         tickets = []
-        for wl, storage, tau, n in items:
-            cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces)
+        for it in items:
+            wl, storage, tau, n = it[:4]
+            eq = it[4] if len(it) > 4 else "series"
+            cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, equilibrium=eq)
             tickets.append(B.lbm_submit(srv, cfg, *_fields(wl), n))
         results = []
-        for (wl, _, _, _), t in zip(items, tickets):
+        for it, t in zip(items, tickets):
+            wl = it[0]
             assert B.lbm_wait(srv, t, timeout) == B.LBM_OK
             S = wl.sites
             out = (np.zeros(S), np.zeros(3 * S), np.zeros(S))
@@ -74,6 +80,11 @@ def _items():
         (W.sod(nx=256, ny=4, nz=4), "f32", W.paper_tau(0.6, "literal"), 40),
         (W.mach2_blob(64, 32, 4, mach=0.5, vortex=0.1), "f16", W.paper_tau(0.55, "literal"), 25),
         (W.smooth_random(33, 5, 4, seed=3, mach=0.3), "bf16", 0.1, 15),
+        # exact entropic equilibrium (Sec. III): the config-5 families in their Mach range
+        (W.mach2_blob(64, 16, 4), "f32", W.paper_tau(0.55, "lb"), 30, "entropic"),
+        (W.mach2_blob(64, 16, 4), "f16", W.paper_tau(0.55, "lb"), 30, "entropic"),
+        (W.sod(nx=128, ny=4, nz=4), "f32", W.paper_tau(0.6, "lb"), 40, "entropic"),
+        (W.taylor_green(16, mach=1.0), "bf16", W.paper_tau(0.55, "lb"), 20, "entropic"),
     ]
 
 
@@ -103,10 +114,12 @@ def test_results_identical_alone_and_in_mix(B):
         for x, y in zip(a, b):
             np.testing.assert_array_equal(x, y)
     # and agrees with the single-case API within the storage's tolerance
-    for (wl, st, tau, n), (_, b) in zip(items, mixed):
-        s0, a = _single(B, wl, st, tau, n)
+    for it, (_, b) in zip(items, mixed):
+        wl, st, tau, n = it[:4]
+        eq = it[4] if len(it) > 4 else "series"
+        s0, a = _single(B, wl, st, tau, n, eq)
         assert s0 == B.LBM_OK
-        assert _rel(a, b, wl.sites) <= _SERVED_VS_SINGLE_TOL[st], (wl.name, st)
+        assert _rel(a, b, wl.sites) <= _SERVED_VS_SINGLE_TOL[st], (wl.name, st, eq)
 
 
 def test_served_case_matches_oracle(B):
@@ -117,6 +130,20 @@ def test_served_case_matches_oracle(B):
     shp = (2, wl.nz, wl.ny, wl.nx)
     ref = O.fields(oracle_run(wl, 30, tau))
     er = field_errors(ref, (r.reshape(shp), u.reshape((3,) + shp), t.reshape(shp)))
+    assert max(er) <= 1e-5, er
+
+
+def test_served_entropic_mach2_matches_oracle(B):
+    """A served Mach-2 blob with the exact entropic equilibrium (Sec. III), FP32 storage, against
+    the FP64 oracle with the same equilibrium: within the FP32 bound of the single-case tests."""
+    wl = W.mach2_blob(32, 16, 4)
+    tau = W.paper_tau(0.55, "lb")
+    (st, (r, u, t)), = _serve(B, [(wl, "f32", tau, 10, "entropic")])[0]
+    assert st == B.LBM_OK
+    shp = (2, wl.nz, wl.ny, wl.nx)
+    ref = O.fields(oracle_run(wl, 10, tau, eq="entropic"))
+    er = field_errors(ref, (r.reshape(shp), u.reshape((3,) + shp), t.reshape(shp)))
+    print("served entropic f32 Mach-2 blob 10 steps: rel err rho %.3g u %.3g theta %.3g" % er)
     assert max(er) <= 1e-5, er
 
 
@@ -145,6 +172,33 @@ def test_admission_respects_budget(B):
         assert B.lbm_poll(srv, 12345)[0] == B.LBM_ENOTFOUND
     finally:
         B.lbm_server_destroy(srv)
+
+
+def test_first_fit_admission_lets_small_cases_pass(B):
+    """When the oldest waiting request does not fit the free budget, a later one that fits is
+    admitted ahead of it: with room for one large case and two small ones, the small cases
+    submitted after a second large one finish before it."""
+    big, small = W.taylor_green(48), W.taylor_green(16)
+    tau = W.paper_tau(0.55, "lb")
+    one_big = B.lbm_footprint(B.make_config(48, 48, 48, tau, "f32"))
+    one_small = B.lbm_footprint(B.make_config(16, 16, 16, tau, "f32"))
+    items = [(big, "f32", tau, 2000), (big, "f32", tau, 50), (small, "f32", tau, 20), (small, "f32", tau, 20)]
+    srv = B.lbm_server_create(one_big + 2 * one_small, 8)
+    try:
+        tickets = [B.lbm_submit(srv, B.make_config(w.nx, w.ny, w.nz, t, st), *_fields(w), n)
+                   for w, st, t, n in items]
+        lat = []
+        for t in tickets:
+            assert B.lbm_wait(srv, t, 300.0) == B.LBM_OK
+            st, l = B.lbm_poll(srv, t)
+            assert st == B.LBM_OK
+            lat.append(l)
+        stats = B.lbm_server_get_stats(srv)
+    finally:
+        B.lbm_server_destroy(srv)
+    assert lat[2] < lat[0] and lat[3] < lat[0]      # the small cases ran beside the first large one
+    assert lat[2] < lat[1] and lat[3] < lat[1]      # ... ahead of the second
+    assert stats["peak_resident_bytes"] <= one_big + 2 * one_small
 
 
 def test_unstable_case_retired_early_others_unaffected(B):

@@ -51,9 +51,27 @@ def test_sod_and_tau_readings():
 
 
 def test_served_mix_deterministic():
-    a = W.served_mix(6, seed=5114)
-    b = W.served_mix(6, seed=5114)
-    assert [(r.workload.name, r.storage, r.nsteps, r.arrival_s) for r in a] == \
-           [(r.workload.name, r.storage, r.nsteps, r.arrival_s) for r in b]
+    a = W.served_mix(24, seed=5114)
+    b = W.served_mix(24, seed=5114)
+    assert [(r.workload.name, r.storage, r.nsteps, r.arrival_s, r.tau) for r in a] == \
+           [(r.workload.name, r.storage, r.nsteps, r.arrival_s, r.tau) for r in b]
     assert all(200 <= r.nsteps <= 2000 and r.storage in ("f32", "f16") for r in a)
     assert all(x.arrival_s < y.arrival_s for x, y in zip(a, a[1:]))
+    assert {r.family for r in a} == {"shock_tube", "taylor_green", "mach2_blob"}
+    assert all(r.equilibrium == "entropic" for r in a)
+    for r in a:
+        wl = r.workload
+        if r.family == "shock_tube":
+            assert (wl.ny, wl.nz) == (4, 4) and 256 <= wl.nx <= 2048 and wl.rho.min() == 0.125
+        elif r.family == "mach2_blob":
+            assert wl.nz == 4 and 256 * 128 <= wl.nx * wl.ny <= 1024 * 256 and wl.faces[0][0] == "eq_inflow"
+        else:
+            assert 32 <= wl.nx <= 192 and r.tau >= 0.05 - 1e-15
+
+
+def test_served_tgv_viscosity_reynolds_400():
+    """nu = tau theta0 (Sec. II) gives Re = U0 (n / 2 pi) / nu = 400 where the floor does not bind."""
+    n, ma = 192, 1.0
+    tau = W.tgv_served_tau(n, ma)
+    assert abs(ma * W.CS * (n / (2 * np.pi)) / (tau * W.THETA0) - 400.0) < 1e-9
+    assert W.tgv_served_tau(32, 0.3) == 0.05
