@@ -281,6 +281,8 @@ typedef struct {
   double busy_seconds;              /* scheduler time spent running ticks */
   double resident_byte_seconds;     /* resident bytes integrated over that time (per tick, the larger of
                                        the counts before and after it): mean resident = this / busy */
+  double backlog_seconds;           /* the part of busy_seconds in ticks that began with requests waiting */
+  double backlog_byte_seconds;      /* resident bytes integrated over backlog_seconds */
 } lbm_server_stats;
 
 /* Creates a server on the current device.  hbm_budget_bytes bounds the resident cases'

@@ -61,7 +61,8 @@ class lbm_server_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong),
                 ("resident_cases", ctypes.c_int), ("resident_bytes", ctypes.c_size_t),
                 ("peak_resident_bytes", ctypes.c_size_t), ("busy_seconds", ctypes.c_double),
-                ("resident_byte_seconds", ctypes.c_double)]
+                ("resident_byte_seconds", ctypes.c_double), ("backlog_seconds", ctypes.c_double),
+                ("backlog_byte_seconds", ctypes.c_double)]
 
 
 def _load():

@@ -557,16 +557,23 @@ void worker_main(lbm_server* s) {
     if (s->active.empty() && s->joining.empty()) continue;
     const auto t0 = Clock::now();
     size_t held = 0;
+    bool backlog = false;  // requests waiting for admission when the tick starts
     {
       std::lock_guard<std::mutex> lk(s->mu);
       held = s->resident_bytes;
+      backlog = !s->queue.empty();
     }
     if (run_tick(s) != LBM_OK) break;
     const auto t1 = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     const double dt = std::chrono::duration<double>(t1 - t0).count();
     s->stats.busy_seconds += dt;
-    s->stats.resident_byte_seconds += dt * static_cast<double>(std::max(held, s->resident_bytes));
+    const double bytes = static_cast<double>(std::max(held, s->resident_bytes));
+    s->stats.resident_byte_seconds += dt * bytes;
+    if (backlog) {
+      s->stats.backlog_seconds += dt;
+      s->stats.backlog_byte_seconds += dt * bytes;
+    }
     s->stats.resident_cases = static_cast<int>(s->active.size());
   }
 }
