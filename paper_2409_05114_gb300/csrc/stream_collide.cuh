@@ -219,9 +219,12 @@ __device__ __forceinline__ float log1p_alpha(float y) {
 }
 __device__ __forceinline__ double log1p_alpha(double y) { return log1p(y); }
 
-// The full-expression solve.  The walk runs once, to collect x_i and w_i F_i in a per-thread
-// (local-memory) array; the sums over directions are then short runtime loops (an unrolled
-// evaluation per iterate would not fit the instruction cache).
+// The full-expression solve.  The walk runs once, to collect x_i and w_i F_i per thread; the
+// sums over directions are then short runtime loops (an unrolled evaluation per iterate would
+// not fit the instruction cache).  FP32 keeps the 2 x 81 values in dynamic shared memory, one
+// column per thread ([2][81][blockDim.x]: consecutive threads, consecutive banks), 648 bytes a
+// thread: in per-thread local memory they overflowed L1 at any useful occupancy and every pass
+// went to L2 (1274 DRAM bytes a site against 648).  FP64 keeps a local array.
 // Each pass expands Delta H about a centre a0 exactly in delta = alpha - a0: with u_i = 1 + a0 x_i,
 // L_i = log u_i and z_i = x_i / u_i,
 //   Delta H(a0 + delta) = F0 + F1 delta + sum_{n>=2} (-1)^n M_n delta^n / (n (n-1)),
@@ -238,11 +241,24 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
   constexpr int N = kDbl ? 10 : 6;
   constexpr int kMaxPass = kDbl ? 40 : 20;
   const R tol = R(kDbl ? 1e-14 : 1e-6);
-  R xs[kQ], wf[kQ];
+  [[maybe_unused]] R xs_local[kDbl ? kQ : 1], wf_local[kDbl ? kQ : 1];
+  R* xs;
+  R* wf;
+  int stride;
+  if constexpr (kDbl) {
+    xs = xs_local;
+    wf = wf_local;
+    stride = 1;
+  } else {
+    extern __shared__ float alpha_smem[];
+    xs = alpha_smem + threadIdx.x;
+    wf = alpha_smem + kQ * blockDim.x + threadIdx.x;
+    stride = blockDim.x;
+  }
   int n = 0;
   visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
-    xs[n] = ratio(E - F, F);
-    wf[n] = wg * F;
+    xs[n * stride] = ratio(E - F, F);
+    wf[n * stride] = wg * F;
     ++n;
   });
   R lo = R(1), hi = amax;
@@ -257,7 +273,7 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
     for (int k = 0; k < N - 1; ++k) M[k] = R(0);
 #pragma unroll 1
     for (int i = 0; i < kQ; ++i) {
-      const R x = xs[i], w = wf[i];
+      const R x = xs[i * stride], w = wf[i * stride];
       if (pass == 0) {
         const R ym = amax * x;
         b += w * x * log1p_alpha(x);
@@ -619,13 +635,21 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 // 4 for FP32/FP16/BF16 storage (<= 128 registers, 16 warps per SM; FP32 with FP64-quality
 // moments too: its double-word sums run at FP32 rates, 9 % faster than at 3 blocks), 3 for
 // FP16/BF16 with FP64 moments (FP64-pipe bound), and no bound for FP64 storage (its 81 doubles
-// need ~250).  The entropic alpha spills at 4 blocks (its 2 x 81 local values do not fit L1 either
-// way) and still runs 7 % (FP32) and 9 % (FP16) faster than at 3: latency hiding decides it.
+// need ~250).  The entropic alpha: 2 blocks, the most its 83 KB of shared memory a block allow
+// (255 registers, no spill).
 template <class Store, bool kF64Mom, int kEq>
 RD3Q81_HD constexpr int sc_min_blocks_128() {
   if constexpr (std::is_same_v<Store, double>) return 1;
   else if constexpr (kF64Mom && !std::is_same_v<Store, float>) return 3;
+  else if constexpr (kEq == kEqEntropicAlpha) return 2;  // shared memory of the alpha solve
   else return 4;
+}
+
+// Dynamic shared memory of the fused kernel: the FP32 alpha solve's 2 x 81 values per thread.
+template <class Store, int kEq, int kBlock>
+constexpr int sc_dyn_smem() {
+  return (kEq == kEqEntropicAlpha && !std::is_same_v<Store, double>) ? 2 * kQ * kBlock * static_cast<int>(sizeof(float))
+                                                                      : 0;
 }
 
 // Threads per block of the fused kernel.  The issue-bound equilibria (exact entropic, exact
@@ -662,17 +686,24 @@ cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   constexpr int kBlock = sc_block<Store, kF64Mom, kEq>();
   const dim3 grid(static_cast<unsigned>((n + kBlock - 1) / kBlock), 2);
+  constexpr int kSmem = sc_dyn_smem<Store, kEq, kBlock>();
   if constexpr (kEq == kEqEntropicAlpha) {
-    // the alpha solve keeps 2 x 81 values per thread in local memory: all of L1 for it (set on
-    // the direct launches; graphs are captured only after those)
+    // the alpha solve keeps 2 x 81 values per thread: in shared memory (FP32; more than the
+    // default 48 KB a block, and the most shared memory the carveout gives) or in local memory
+    // (FP64; then all of L1 for it).  Set on the direct launches; graphs are captured only after
+    // those.
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaError_t e = cudaStreamIsCapturing(s, &cs);
-    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       e = cudaFuncSetAttribute(stream_collide_kernel<Store, kF64Mom, kEq, kKind>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+                               cudaFuncAttributePreferredSharedMemoryCarveout, kSmem > 0 ? 100 : 0);
+      if (e == cudaSuccess && kSmem > 0)
+        e = cudaFuncSetAttribute(stream_collide_kernel<Store, kF64Mom, kEq, kKind>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    }
     if (e != cudaSuccess) return e;
   }
-  stream_collide_kernel<Store, kF64Mom, kEq, kKind><<<grid, kBlock, 0, s>>>(p);
+  stream_collide_kernel<Store, kF64Mom, kEq, kKind><<<grid, kBlock, kSmem, s>>>(p);
   return cudaGetLastError();
 }
 
