@@ -49,6 +49,8 @@ def parse():
                    help="for --quick runs: two buffers, or one buffer updated in place (AA)")
     p.add_argument("--collision", default="bgk", choices=["bgk", "entropic"],
                    help="for --quick runs: BGK (alpha = 2) or the entropic alpha (needs --equilibrium entropic)")
+    p.add_argument("--fp64-moments", action="store_true",
+                   help="for --quick runs: FP64-quality (double-word) moment sums and temperature recovery")
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-only", type=int, default=0, metavar="K",
@@ -697,8 +699,8 @@ def ours(args):
 
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(gpu_index_for_smi(local))
-    head = run_case(B, args.n, args.storage, args.steps, args.warmup, world, sampler=sampler, eq=args.equilibrium,
-                    collision=args.collision, streaming=args.streaming)
+    head = run_case(B, args.n, args.storage, args.steps, args.warmup, world, fp64_moments=args.fp64_moments,
+                    sampler=sampler, eq=args.equilibrium, collision=args.collision, streaming=args.streaming)
     value = head["mlups"] * world
     achieved = head["gbs"]
     line = {
@@ -727,6 +729,9 @@ def ours(args):
                                           ("tgv512_f16", 512, "f16", False, "series", "bgk", "pingpong"),
                                           ("tgv512_bf16", 512, "bf16", False, "series", "bgk", "pingpong"),
                                           ("tgv512_f32_fp64moments", 512, "f32", True, "series", "bgk", "pingpong"),
+                                          ("tgv512_f16_fp64moments", 512, "f16", True, "series", "bgk", "pingpong"),
+                                          ("tgv512_bf16_fp64moments", 512, "bf16", True, "series", "bgk", "pingpong"),
+                                          ("tgv512_f32_aa_fp64moments", 512, "f32", True, "series", "bgk", "aa"),
                                           ("tgv512_f32_exactw", 512, "f32", False, "series_exact_w", "bgk", "pingpong"),
                                           ("tgv512_f32_entropic", 512, "f32", False, "entropic", "bgk", "pingpong"),
                                           ("tgv512_f16_entropic", 512, "f16", False, "entropic", "bgk", "pingpong"),

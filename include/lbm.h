@@ -124,9 +124,10 @@ typedef struct {
                          on the two x faces only; y and z must be periodic. */
   int storage;        /* lbm_storage */
   int fp64_moments;   /* 1: moment sums and temperature recovery to FP64 quality for FP32/FP16/
-                         BF16 storage (no effect for LBM_F64): FP32 storage by cascaded
-                         double-word (float + float, ~2^-48 relative) sums at FP32 rates, FP16/BF16
-                         storage in FP64; 0: FP32 */
+                         BF16 storage (no effect for LBM_F64), by cascaded double-word (float +
+                         float, ~2^-48 relative) sums at FP32 rates: FP32 storage over the 81
+                         values, FP16/BF16 over each shell's offsets, weighted by the shell's
+                         weights held as double words; 0: FP32 */
   void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
                          creates its own stream (which synchronises with the legacy
                          default stream) */
@@ -136,7 +137,7 @@ typedef struct {
   int collision;      /* lbm_collision.  LBM_COLLISION_ENTROPIC needs equilibrium =
                          LBM_EQ_ENTROPIC.  A site with a population <= 0 (where H is not
                          defined) takes alpha = 2. */
-  int streaming;      /* lbm_streaming.  LBM_STREAM_AA needs fp64_moments = 0. */
+  int streaming;      /* lbm_streaming */
 } lbm_config;
 
 /* Device bytes lbm_create would allocate for this configuration (both population buffers

@@ -57,8 +57,6 @@ lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why) {
     return *why = "fp64_moments is available with the series equilibrium (LBM_EQ_SERIES) only", LBM_EINVAL;
   if (cfg->streaming != LBM_STREAM_PINGPONG && cfg->streaming != LBM_STREAM_AA)
     return *why = "streaming must be LBM_STREAM_PINGPONG or LBM_STREAM_AA", LBM_EINVAL;
-  if (cfg->streaming == LBM_STREAM_AA && cfg->fp64_moments)
-    return *why = "AA streaming is available with fp64_moments = 0", LBM_EINVAL;
   if (cfg->collision != LBM_COLLISION_BGK && cfg->collision != LBM_COLLISION_ENTROPIC)
     return *why = "collision must be LBM_COLLISION_BGK or LBM_COLLISION_ENTROPIC", LBM_EINVAL;
   if (cfg->collision == LBM_COLLISION_ENTROPIC && cfg->equilibrium != LBM_EQ_ENTROPIC)
@@ -426,7 +424,7 @@ cudaError_t launch_step_kernel(lbm_ctx* ctx, int cur, int kind, cudaStream_t s, 
     p.z1 = z1;
   }
   ++*launches;
-  return lbm::launch_stream_collide(ctx->storage, kind == lbm::kStepPingPong ? ctx->cfg.fp64_moments : 0,
+  return lbm::launch_stream_collide(ctx->storage, ctx->cfg.fp64_moments,
                                     step_mode(ctx), kind, p, s);
 }
 

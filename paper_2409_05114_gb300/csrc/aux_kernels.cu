@@ -624,12 +624,12 @@ cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, int kin
                                   cudaStream_t s) {
   if (p.z0 < 0 || p.z1 > p.g.nz) return cudaErrorInvalidValue;
   if (kind != kStepPingPong) {
-    if (fp64_moments) return cudaErrorInvalidValue;
+    if (fp64_moments && eq != kEqSeries) return cudaErrorInvalidValue;
     switch (storage) {
-      case kF64: return launch_sc_aa_f64(eq, kind, p, s);
-      case kF32: return launch_sc_aa_f32(eq, kind, p, s);
-      case kF16Off: return launch_sc_aa_f16(eq, kind, p, s);
-      case kBF16Off: return launch_sc_aa_bf16(eq, kind, p, s);
+      case kF64: return launch_sc_aa_f64(fp64_moments, eq, kind, p, s);
+      case kF32: return launch_sc_aa_f32(fp64_moments, eq, kind, p, s);
+      case kF16Off: return launch_sc_aa_f16(fp64_moments, eq, kind, p, s);
+      case kBF16Off: return launch_sc_aa_bf16(fp64_moments, eq, kind, p, s);
       default: return cudaErrorInvalidValue;
     }
   }

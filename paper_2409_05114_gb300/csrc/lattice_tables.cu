@@ -75,9 +75,16 @@ void build_lattice_tables(LatticeTables* t) {
     const int a[3] = {kDirs[i].hx, kDirs[i].hy, kDirs[i].hz};
     for (int c = 0; c < 3; ++c) kmax[kDirs[i].shell] = std::max(kmax[kDirs[i].shell], std::abs(a[c]));
   }
+  auto split = [](double v, float* out) {
+    out[0] = static_cast<float>(v);
+    out[1] = static_cast<float>(v - static_cast<double>(out[0]));
+  };
   for (int s = 0; s < kShells; ++s) {
     t->wc2f[s] = static_cast<float>(w[s] * kShellC2[s]);
     t->whkf[s] = static_cast<float>(w[s] * 0.5 * kmax[s]);
+    split(w[s], t->w_dw[s]);
+    split(w[s] * kShellC2[s], t->wc2_dw[s]);
+    split(w[s] * 0.5 * kmax[s], t->whk_dw[s]);
   }
   for (int i = 0; i < kQ; ++i) t->wdir[i] = w[kDirs[i].shell];
   for (int i = 0; i < kQ; ++i) {

@@ -43,6 +43,8 @@ struct LatticeTables {
   float theta0x3_dw[2];  // 3 theta0 as a double word hi + lo (moment read-back of offset storage)
   float wc2f[kShells];   // w_s c_s^2 (moment sums of offset storage)
   float whkf[kShells];   // w_s k_s / 2, k_s the nonzero |h_a| of shell s (momentum sums)
+  // the same three and w_s as double words hi + lo (FP64-quality moment sums of offset storage)
+  float w_dw[kShells][2], wc2_dw[kShells][2], whk_dw[kShells][2];
   double wdir[kQ];  // w_i per direction (decoding offset storage in the auxiliary kernels)
   // In-place (AA) streaming: opp[i] = index of -c_i; the site that pulls f_i from site n of
   // sublattice s is n - push_d[s][i][0..2] on sublattice push_d[s][i][3].
@@ -147,16 +149,16 @@ inline size_t storage_bytes(int s) { return s == kF64 ? 8 : s == kF32 ? 4 : 2; }
 // eq: kEqSeries (App. B equilibrium, BGK), kEqSeriesExactW (the same with the exact
 // temperature weights of Eq. (zeroveleq)), kEqEntropic (exact entropic equilibrium of Sec. III,
 // BGK) or kEqEntropicAlpha (exact entropic equilibrium, entropic alpha of Eq. (delH)).
-// kind: StepKind (AA kinds in the sc_aa_*.cu units; they take fp64_moments = 0).
+// kind: StepKind (AA kinds in the sc_aa_*.cu units).
 cudaError_t launch_stream_collide(int storage, int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f64(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f32(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_f16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
 cudaError_t launch_sc_bf16(int fp64_moments, int eq, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_aa_f64(int eq, int kind, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_aa_f32(int eq, int kind, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_aa_f16(int eq, int kind, const StepParams& p, cudaStream_t s);
-cudaError_t launch_sc_aa_bf16(int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f64(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f32(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_f16(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
+cudaError_t launch_sc_aa_bf16(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s);
 
 // Auxiliary kernels (aux_kernels.cu).  `layout` (StateLayout) says where the stored state
 // keeps each population; own_slots = 1 writes the initial state in the AA own layout.

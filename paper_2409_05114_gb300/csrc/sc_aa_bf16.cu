@@ -5,8 +5,8 @@
 
 namespace lbm {
 
-cudaError_t launch_sc_aa_bf16(int eq, int kind, const StepParams& p, cudaStream_t s) {
-  return launch_sc_aa_all<__nv_bfloat16>(eq, kind, p, s);
+cudaError_t launch_sc_aa_bf16(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s) {
+  return launch_sc_aa_all<__nv_bfloat16>(fp64_moments, eq, kind, p, s);
 }
 
 }  // namespace lbm

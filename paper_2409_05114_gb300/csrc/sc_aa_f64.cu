@@ -5,8 +5,8 @@
 
 namespace lbm {
 
-cudaError_t launch_sc_aa_f64(int eq, int kind, const StepParams& p, cudaStream_t s) {
-  return launch_sc_aa_all<double>(eq, kind, p, s);
+cudaError_t launch_sc_aa_f64(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s) {
+  return launch_sc_aa_all<double>(fp64_moments, eq, kind, p, s);
 }
 
 }  // namespace lbm

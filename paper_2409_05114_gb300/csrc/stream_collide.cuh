@@ -120,10 +120,54 @@ __device__ __forceinline__ Moments<Dw> site_moments_dw(const float* f) {
   return Moments<Dw>{fast_two_sum(pr, qr), two_sum(px, qx), two_sum(py, qy), two_sum(pz, qz), fast_two_sum(pe, qe)};
 }
 
+// Offset storage with FP64-quality moments: rho = 1 + sum_s w_s S_s, <f, c^2> = 3 theta0 + sum_s
+// w_s c_s^2 S_s and j_a = sum_s (w_s k_s / 2) J_a,s, where S_s sums the offsets of shell s and
+// J_a,s their signed sum over the members with h_a != 0 (every such component is +-k_s / 2).
+// The shell sums are cascaded (Sum2: each TwoSum's error collects in a second float), multiplied
+// by the shell's weights held as double words, and the products accumulated the same way: the
+// double-word scheme of site_moments_dw with the weights' rounding removed too.
+__device__ __forceinline__ Moments<Dw> site_moments_dw_offset(const float* d, const LatticeTables& tb) {
+  auto acc = [](float& p, float& q, Dw v) {  // p + q += v
+    const Dw t = two_sum(p, v.hi);
+    p = t.hi;
+    q = __fadd_rn(q, __fadd_rn(t.lo, v.lo));
+  };
+  auto wmul = [](Dw a, const float* w) { return dw_mul(a, Dw{w[0], w[1]}); };
+  float pr = 0.0f, qr = 0.0f, pe = 0.0f, qe = 0.0f, px = 0.0f, qx = 0.0f, py = 0.0f, qy = 0.0f, pz = 0.0f, qz = 0.0f;
+  acc(pr, qr, wmul(Dw{d[0], 0.0f}, tb.w_dw[0]));
+  float sp = 0.0f, sq = 0.0f, xp = 0.0f, xq = 0.0f, yp = 0.0f, yq = 0.0f, zp = 0.0f, zq = 0.0f;
+  static_for<kPairs>([&](auto Pc) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr rd3q81::Dir dd = rd3q81::kDirs[1 + 2 * P];
+    constexpr int s = dd.shell;
+    constexpr bool last = P == kPairs - 1 || rd3q81::kDirs[3 + 2 * P].shell != s;
+    const float fp = d[1 + 2 * P], fm = d[2 + 2 * P];
+    const Dw sum = two_sum(fp, fm), dif = two_sum(fp, -fm);
+    const Dw ndif{-dif.hi, -dif.lo};
+    acc(sp, sq, sum);
+    if constexpr (dd.hx != 0) acc(xp, xq, dd.hx > 0 ? dif : ndif);
+    if constexpr (dd.hy != 0) acc(yp, yq, dd.hy > 0 ? dif : ndif);
+    if constexpr (dd.hz != 0) acc(zp, zq, dd.hz > 0 ? dif : ndif);
+    if constexpr (last) {
+      const Dw S = two_sum(sp, sq);
+      acc(pr, qr, wmul(S, tb.w_dw[s]));
+      acc(pe, qe, wmul(S, tb.wc2_dw[s]));
+      acc(px, qx, wmul(two_sum(xp, xq), tb.whk_dw[s]));
+      acc(py, qy, wmul(two_sum(yp, yq), tb.whk_dw[s]));
+      acc(pz, qz, wmul(two_sum(zp, zq), tb.whk_dw[s]));
+      sp = sq = xp = xq = yp = yq = zp = zq = 0.0f;
+    }
+  });
+  return Moments<Dw>{dw_add(two_sum(pr, qr), 1.0f), two_sum(px, qx), two_sum(py, qy), two_sum(pz, qz),
+                     dw_add(two_sum(pe, qe), Dw{tb.theta0x3_dw[0], tb.theta0x3_dw[1]})};
+}
+
 template <class Store, bool kF64Mom>
 __device__ __forceinline__ auto site_moments(const typename Codec<Store>::Real* f, const LatticeTables& tb) {
   if constexpr (kF64Mom && std::is_same_v<Store, float>) {
     return site_moments_dw(f);
+  } else if constexpr (kF64Mom && Codec<Store>::kOffset) {
+    return site_moments_dw_offset(f, tb);
   } else {
   using C = Codec<Store>;
   using R = typename C::Real;
@@ -632,15 +676,14 @@ __device__ __forceinline__ void site_update_slabs(const StepParams& p, int t) {
 }
 
 // Resident blocks per SM the compiler must fit (register budget 65536 / (blocks * 128)):
-// 4 for FP32/FP16/BF16 storage (<= 128 registers, 16 warps per SM; FP32 with FP64-quality
-// moments too: its double-word sums run at FP32 rates, 9 % faster than at 3 blocks), 3 for
-// FP16/BF16 with FP64 moments (FP64-pipe bound), and no bound for FP64 storage (its 81 doubles
+// 4 for FP32/FP16/BF16 storage (<= 128 registers, 16 warps per SM; with FP64-quality moments
+// too: their double-word sums run at FP32 rates, 9 % faster than at 3 blocks for FP32), and no
+// bound for FP64 storage (its 81 doubles
 // need ~250).  The entropic alpha: 2 blocks, the most its 83 KB of shared memory a block allow
 // (255 registers, no spill).
 template <class Store, bool kF64Mom, int kEq>
 RD3Q81_HD constexpr int sc_min_blocks_128() {
   if constexpr (std::is_same_v<Store, double>) return 1;
-  else if constexpr (kF64Mom && !std::is_same_v<Store, float>) return 3;
   else if constexpr (kEq == kEqEntropicAlpha) return 2;  // shared memory of the alpha solve
   else return 4;
 }
@@ -708,14 +751,16 @@ cudaError_t launch_sc(const StepParams& p, cudaStream_t s) {
 }
 
 // Both AA kinds of one storage and equilibrium (the sc_aa_*.cu units).
-template <class Store, int kEq>
+template <class Store, int kEq, bool kF64Mom = false>
 cudaError_t launch_sc_aa(int kind, const StepParams& p, cudaStream_t s) {
-  return kind == kStepAAOwn ? launch_sc<Store, false, kEq, kStepAAOwn>(p, s)
-                            : launch_sc<Store, false, kEq, kStepAANeighbour>(p, s);
+  return kind == kStepAAOwn ? launch_sc<Store, kF64Mom, kEq, kStepAAOwn>(p, s)
+                            : launch_sc<Store, kF64Mom, kEq, kStepAANeighbour>(p, s);
 }
 
+// FP64-quality moments are offered with the series equilibrium.
 template <class Store>
-cudaError_t launch_sc_aa_all(int eq, int kind, const StepParams& p, cudaStream_t s) {
+cudaError_t launch_sc_aa_all(int fp64_moments, int eq, int kind, const StepParams& p, cudaStream_t s) {
+  if (fp64_moments) return eq == kEqSeries ? launch_sc_aa<Store, kEqSeries, true>(kind, p, s) : cudaErrorInvalidValue;
   switch (eq) {
     case kEqSeries: return launch_sc_aa<Store, kEqSeries>(kind, p, s);
     case kEqSeriesExactW: return launch_sc_aa<Store, kEqSeriesExactW>(kind, p, s);

@@ -93,7 +93,7 @@ def test_bad_face_kind_rejected(B):
 
 def test_equilibrium_and_collision_validation(B):
     for kw in (dict(equilibrium="entropic", collision="entropic"), dict(equilibrium="series_exact_w"),
-               dict(equilibrium="series", fp64_moments=True)):
+               dict(equilibrium="series", fp64_moments=True), dict(fp64_moments=True, streaming="aa")):
         assert B.lbm_footprint(B.make_config(16, 8, 4, 0.1, "f32", **kw)) > 0
     for kw in (dict(equilibrium="series", collision="entropic"),            # alpha needs the exact equilibrium
                dict(equilibrium="series_exact_w", collision="entropic"),

@@ -119,3 +119,65 @@ def test_reciprocal_and_products():
         x = fast_two_sum(f32(xv), f32(xv - np.float64(f32(xv))))
         m = dw_mul(x, y)
         assert abs(val(m) - val(x) * val(y)) <= 8 * EPS2 * abs(val(x) * val(y))
+
+
+def test_offset_moments_near_fp64_sums():
+    """The step's site_moments_dw_offset (FP16/BF16 offset storage, d = f/w - 1): per shell the
+    offsets are summed by cascaded TwoSum (S_s, and the signed J_a,s over members with h_a != 0),
+    each shell sum is multiplied by the shell's weights held as double words (w_s, w_s c_s^2,
+    w_s k_s / 2) and the products accumulated the same way.  Over FP16-representable offsets of
+    random sites the result equals the FP64 sums rho = 1 + <w, d>, j = <w, d c>,
+    <f, c^2> = 3 theta0 + <w, d c^2> to a few units of 2^-48 of their scale."""
+    lat = O.velocity_set()
+    h, w, q = lat.h, lat.w, lat.q
+    opp = [int(np.flatnonzero(np.all(h == -h[i], axis=1))[0]) for i in range(q)]
+    rest = int(np.flatnonzero(np.all(h == 0, axis=1))[0])
+    c2 = (h.astype(np.float64) ** 2).sum(1) / 4.0
+    kmax = np.abs(h).max(axis=1)
+    # +/- pairs grouped by shell (shell = (|c|^2, nonzero pattern): the same weight)
+    pairs, seen = [], {rest}
+    for i in range(q):
+        if i not in seen:
+            pairs.append((i, opp[i]))
+            seen |= {i, opp[i]}
+    shells = {}
+    for i, j in pairs:
+        shells.setdefault(round(w[i], 15), []).append((i, j))
+
+    def split(v):
+        hi = f32(v)
+        return hi, f32(v - np.float64(hi))
+
+    def acc(pq, v):
+        t0, t1 = two_sum(pq[0], v[0])
+        return [t0, f32(pq[1] + f32(t1 + v[1]))]
+
+    rng = np.random.default_rng(3)
+    worst = 0.0
+    for _ in range(200):
+        d = np.float16(rng.normal(size=q) * 10 ** rng.uniform(-3, 0.7, q)).astype(f32)
+        tot = {k: [f32(0), f32(0)] for k in ("r", "e", "x", "y", "z")}
+        tot["r"] = acc(tot["r"], dw_mul((d[rest], f32(0)), split(w[rest])))
+        for members in shells.values():
+            i0 = members[0][0]
+            S = {k: [f32(0), f32(0)] for k in ("s", "x", "y", "z")}
+            for i, j in members:
+                s, df = two_sum(d[i], d[j]), two_sum(d[i], f32(-d[j]))
+                S["s"] = acc(S["s"], s)
+                for a, key in enumerate("xyz"):
+                    if h[i][a]:
+                        S[key] = acc(S[key], df if h[i][a] > 0 else (f32(-df[0]), f32(-df[1])))
+            ws, wc2, whk = split(w[i0]), split(w[i0] * c2[i0]), split(w[i0] * 0.5 * kmax[i0])
+            tot["r"] = acc(tot["r"], dw_mul(two_sum(*S["s"]), ws))
+            tot["e"] = acc(tot["e"], dw_mul(two_sum(*S["s"]), wc2))
+            for key in "xyz":
+                tot[key] = acc(tot[key], dw_mul(two_sum(*S[key]), whk))
+        got = [1.0 + val(two_sum(*tot["r"]))] + [val(two_sum(*tot[k])) for k in "xyz"] + \
+              [3.0 * lat.theta0 + val(two_sum(*tot["e"]))]
+        dd, c = d.astype(np.float64), h / 2.0
+        ref = [1.0 + (w * dd).sum()] + [(w * c[:, a] * dd).sum() for a in range(3)] + \
+              [3.0 * lat.theta0 + (w * c2 * dd).sum()]
+        scale = [1.0 + np.abs(w * dd).sum()] + [np.abs(w * c[:, a] * dd).sum() for a in range(3)] + \
+                [3.0 * lat.theta0 + np.abs(w * c2 * dd).sum()]
+        worst = max(worst, max(abs(g - r) / s for g, r, s in zip(got, ref, scale)))
+    assert worst <= 16 * EPS2, worst

@@ -28,9 +28,9 @@ def _fields(wl):
             np.ascontiguousarray(wl.theta, dtype=np.float64).reshape(-1))
 
 
-def _run(B, wl, tau, storage, steps, streaming, eq="series", collision="bgk"):
+def _run(B, wl, tau, storage, steps, streaming, eq="series", collision="bgk", fp64_moments=False):
     cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, wl.faces, equilibrium=eq, collision=collision,
-                        streaming=streaming)
+                        streaming=streaming, fp64_moments=fp64_moments)
     ctx = B.lbm_create(cfg)
     out = []
     try:
@@ -50,7 +50,7 @@ def _run(B, wl, tau, storage, steps, streaming, eq="series", collision="bgk"):
     return out
 
 
-_TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3}
+_TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 1.6e-2}
 
 
 def _same(a, b, storage):
@@ -131,3 +131,16 @@ def test_aa_diagnostics(B):
         finally:
             B.lbm_destroy(ctx)
     np.testing.assert_allclose(vals[0], vals[1], rtol=1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_aa_fp64_moments_matches_pingpong(B, storage):
+    """FP64-quality moment sums (double words) with in-place streaming, against ping-pong with the
+    same option, over every boundary kind's case."""
+    for name, make, reading in CASES:
+        wl = make()
+        tau = wl.paper_tau(reading)
+        steps = [1, 2, 12]
+        a = _run(B, wl, tau, storage, steps, "aa", fp64_moments=True)
+        b = _run(B, wl, tau, storage, steps, "pingpong", fp64_moments=True)
+        _same(a, b, storage)
