@@ -467,7 +467,7 @@ __device__ __forceinline__ void site_relax(typename Codec<Store>::Real* f, const
   } else {
     constexpr bool kDbl = std::is_same_v<R, double>;
     const R T[5] = {rh, R(mo.jx), R(mo.jy), R(mo.jz), R(mo.E)};
-    if (!entropic_multipliers<R>(T, mux, muy, muz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 6, tb, lam))
+    if (!entropic_multipliers<R>(T, mux, muy, muz, theta, R(kDbl ? 1e-13 : 1e-6), kDbl ? 30 : 16, tb, lam))
       atomicOr(flag, 1u);
   }
 

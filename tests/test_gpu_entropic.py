@@ -73,6 +73,21 @@ def test_mach2_blob_runs_with_entropic_equilibrium(B):
     assert np.all(np.isfinite(r)) and np.all(t > 0)
 
 
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("f16", 1e-2)])
+def test_mach2_blob_parity_instance(B, storage, tol):
+    """The Mach-2 blob's parity instance, 128 x 32 x 4: the vortex fills the periodic y extent and
+    reaches Mach 2.6 at theta = 0.67 theta0, where the multipliers' Newton needs more than 6 FP32
+    evaluations (with 6 the FP32 run drifted to O(1) errors and failed within 10 steps).  Ten
+    steps against the FP64 oracle with the exact entropic equilibrium."""
+    wl = W.mach2_blob(128, 32, 4)
+    tau = wl.paper_tau("lb")
+    ref = O.fields(oracle_run(wl, 10, tau, eq="entropic"))
+    _, r, u, t = gpu_run(wl, 10, tau, storage, eq="entropic", check_stable=True)
+    er = field_errors(ref, (r, u, t))
+    print("entropic %s Mach-2 blob 128x32x4 10 steps: rel err rho %.3g u %.3g theta %.3g" % (storage, *er))
+    assert max(er) <= tol, er
+
+
 def test_strong_sod_entropic_matches_riemann(B):
     """The Sod tube under the tau_lb reading (omega = 1.67) blows up with the series
     equilibrium within ~20 steps; with the exact equilibrium the FP32 GPU run follows the
