@@ -70,16 +70,17 @@ struct CaseSlabs {
   void* dst[2][kQ];
 };
 
-// Step k of the current tick for the resident cases of one group (storage type S, equilibrium
-// kEq): one kernel per group, so each holds one site update (a kernel with several overflowed the
-// instruction cache).  Grid: persistent (SMs x resident blocks); block b handles tiles b,
-// b + gridDim.x, ...  No block waits on another.
-// Tiles [0, half) are the P sublattice of every case of the group, [half, 2 half) the R
-// sublattice: blocks working side by side then mostly run one of the two compiled site updates.
-// When a block's tile belongs to another (case, parity, sublattice) than its last one, the block
-// copies that case's 2 x 81 slab bases into shared memory; the site update then reads them
-// there, as the single-case kernel reads its kernel parameters.
-template <class S, int kEq>
+// Step k of the current tick, sublattice SUB, for the resident cases of one group (storage type S,
+// equilibrium kEq): one kernel per group and sublattice, so each holds one site update.  A kernel
+// with several (the three storage types once, then both sublattices) overflowed the instruction
+// cache: with the entropic update, 6.7 "no instruction" stalls per issue against 1.0 for the
+// single-case kernel, whose blocks each run one sublattice.  Grid: persistent (SMs x resident
+// blocks); block b handles tiles b, b + gridDim.x, ... of the group's packed tiles (`half` of them
+// per sublattice).  No block waits on another.  When a block's tile belongs to another
+// (case, parity) than its last one, the block copies that case's 81 source and 81 destination
+// slab bases into shared memory; the site update then reads them there, as the single-case
+// kernel reads its kernel parameters.
+template <class S, int kEq, int SUB>
 __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc* __restrict__ cases,
                                                                const CaseSlabs* __restrict__ slabs, int ncases,
                                                                long long half, int k, const LatticeTables tab) {
@@ -88,32 +89,27 @@ __global__ void __launch_bounds__(kScBlock, 4) served_step_kernel(const CaseDesc
   __shared__ void* s_dst[kQ];
   for (int c = threadIdx.x; c < ncases; c += blockDim.x) s_first[c] = cases[c].tile0;
   __syncthreads();
-  int have = -1;  // (case, parity, sublattice) whose slab bases are in shared memory
-  for (long long tile = blockIdx.x; tile < 2 * half; tile += gridDim.x) {
-    const int sub = tile >= half ? 1 : 0;
-    const long long ptile = tile - sub * half;
-    const int c = find_case(s_first, ncases, ptile);
+  int have = -1;  // (case, parity) whose slab bases are in shared memory
+  for (long long tile = blockIdx.x; tile < half; tile += gridDim.x) {
+    const int c = find_case(s_first, ncases, tile);
     const CaseDesc& cd = cases[c];
     const int par = (cd.parity + k) & 1;
-    const int key = (2 * c + par) * 2 + sub;
+    const int key = 2 * c + par;
     if (key != have) {  // the same for every thread of the block
       __syncthreads();
-      const CaseSlabs& tb = slabs[2 * c + par];
+      const CaseSlabs& tb = slabs[key];
       for (int i = threadIdx.x; i < kQ; i += blockDim.x) {
-        s_src[i] = tb.src[sub][i];
-        s_dst[i] = tb.dst[sub][i];
+        s_src[i] = tb.src[SUB][i];
+        s_dst[i] = tb.dst[SUB][i];
       }
       __syncthreads();
       have = key;
     }
-    const long long t = (ptile - cd.tile0) * kScBlock + threadIdx.x;
+    const long long t = (tile - cd.tile0) * kScBlock + threadIdx.x;
     const long long n = static_cast<long long>(cd.g.nx) * cd.g.ny * cd.g.nz;
     if (t >= n) continue;
-    const SharedSlabs sl{s_src, s_dst};
-    if (sub == 0)
-      site_update_table<S, false, 0, kEq, kStepPingPong>(cd.g, cd.omega, cd.flag, tab, sl, static_cast<int>(t));
-    else
-      site_update_table<S, false, 1, kEq, kStepPingPong>(cd.g, cd.omega, cd.flag, tab, sl, static_cast<int>(t));
+    site_update_table<S, false, SUB, kEq, kStepPingPong>(cd.g, cd.omega, cd.flag, tab, SharedSlabs{s_src, s_dst},
+                                                         static_cast<int>(t));
   }
 }
 
@@ -125,13 +121,15 @@ constexpr int kGroupEq[kGroups] = {kEqSeries, kEqSeries, kEqSeries, kEqEntropic,
 struct TickPlan {
   int first[kGroups] = {};      // first case of the group in the table
   int count[kGroups] = {};
-  long long tiles[kGroups] = {};  // P-sublattice tiles of the group (the R half is as many)
+  long long tiles[kGroups] = {};  // tiles of the group per sublattice
 };
 
+// Both sublattices of one step of a group: the P kernel, then the R kernel.
 template <class S, int kEq>
 void launch_served(const CaseDesc* d, const CaseSlabs* sl, int count, long long tiles, int k, const LatticeTables& tab,
                    int grid, cudaStream_t s) {
-  served_step_kernel<S, kEq><<<grid, kScBlock, 0, s>>>(d, sl, count, tiles, k, tab);
+  served_step_kernel<S, kEq, 0><<<grid, kScBlock, 0, s>>>(d, sl, count, tiles, k, tab);
+  served_step_kernel<S, kEq, 1><<<grid, kScBlock, 0, s>>>(d, sl, count, tiles, k, tab);
 }
 
 void launch_group(int gi, const CaseDesc* d, const CaseSlabs* sl, int count, long long tiles, int k,
@@ -378,7 +376,7 @@ cudaGraphExec_t tick_graph(lbm_server* s, int ncases, const TickPlan& plan, long
     }
     for (int gi = 0; gi < kGroups; ++gi) {
       if (plan.count[gi] == 0) continue;
-      const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, 2 * plan.tiles[gi]));
+      const int grid = static_cast<int>(std::min<long long>(s->grid_blocks, plan.tiles[gi]));
       launch_group(gi, s->d_cases + plan.first[gi], s->d_slabs + 2 * plan.first[gi], plan.count[gi], plan.tiles[gi], k,
                    s->tab, grid, cap);
     }
@@ -515,7 +513,7 @@ lbm_status run_tick(lbm_server* s) {
   ++s->stats.graph_launches;
   int groups = 0;
   for (int gi = 0; gi < kGroups; ++gi) groups += plan.count[gi] > 0;
-  s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + groups);
+  s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + 2 * groups);
   ++s->stats.ticks;
   SRV_CK(s, cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(unsigned int) * s->max_cases, cudaMemcpyDeviceToHost,
                             s->compute));
@@ -620,7 +618,7 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
   cudaMemset(s->d_flags, 0, sizeof(unsigned int) * max_cases);
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel<float, kEqSeries>, kScBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, served_step_kernel<float, kEqSeries, 0>, kScBlock, 0);
   s->grid_blocks = std::max(1, sms * std::max(1, per_sm));
   s->worker = std::thread(worker_main, s);
   *out = s;
