@@ -104,7 +104,8 @@ void fill_slab_bases(StepParams* p, size_t elem, int kind = kStepPingPong);
 lbm_status plan_geometry(const lbm_config* cfg, Geometry* g, std::string* why);
 
 // Storage codecs.  FP64 / FP32 store f_i itself.  FP16 / BF16 store the offset
-// d_i = f_i / w_i - 1 (f_i = w_i (1 + d_i)); the collide then works on d directly.
+// d_i = f_i / w_i - 1 (f_i = w_i (1 + d_i)); the collide then works on d directly.  store_evict_first
+// stores with the evict-first cache hint (st.global.cs; the in-place AA steps).
 template <class S>
 struct Codec;
 template <>
@@ -113,6 +114,7 @@ struct Codec<double> {
   static constexpr bool kOffset = false;
   static __device__ __forceinline__ double load(const double* p) { return *p; }
   static __device__ __forceinline__ void store(double* p, double v) { *p = v; }
+  static __device__ __forceinline__ void store_evict_first(double* p, double v) { __stcs(p, v); }
 };
 template <>
 struct Codec<float> {
@@ -120,6 +122,7 @@ struct Codec<float> {
   static constexpr bool kOffset = false;
   static __device__ __forceinline__ float load(const float* p) { return *p; }
   static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+  static __device__ __forceinline__ void store_evict_first(float* p, float v) { __stcs(p, v); }
 };
 template <>
 struct Codec<__half> {
@@ -127,6 +130,7 @@ struct Codec<__half> {
   static constexpr bool kOffset = true;
   static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p); }
   static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ void store_evict_first(__half* p, float v) { __stcs(p, __float2half_rn(v)); }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -134,6 +138,9 @@ struct Codec<__nv_bfloat16> {
   static constexpr bool kOffset = true;
   static __device__ __forceinline__ float load(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ void store_evict_first(__nv_bfloat16* p, float v) {
+    __stcs(p, __float2bfloat16_rn(v));
+  }
 };
 
 // Storage kinds (values match lbm_storage in include/lbm.h).

@@ -666,7 +666,13 @@ __device__ __forceinline__ void site_update_table(const Geometry& g, double omeg
     constexpr int dx = kPush ? rd3q81::pull_disp(-d.hx, SUB) : 0;
     constexpr int dy = kPush ? rd3q81::pull_disp(-d.hy, SUB) : 0;
     constexpr int dz = kPush ? rd3q81::pull_disp(-d.hz, SUB) : 0;
-    C::store(static_cast<Store*>(sl.dst(i)) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]), f[i]);
+    Store* q = static_cast<Store*>(sl.dst(i)) + (zs[dz + 4] + ys[dy + 4] + xs[dx + 4]);
+    // In-place (AA) steps store with the evict-first hint (st.global.cs): FP32 7232 -> 7473 MLUPS at
+    // TGV 512^3.  Ping-pong lost with it (FP32 8818 -> 8602, FP16 14940 -> 14668): plain stores.
+    if constexpr (kKind != kStepPingPong)
+      C::store_evict_first(q, f[i]);
+    else
+      C::store(q, f[i]);
   });
 }
 
