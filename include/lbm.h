@@ -265,9 +265,11 @@ lbm_status lbm_totals_noalloc(const void* f, int storage, int nx, int ny, int nz
  * free and the sum of resident case footprints (2 population buffers each) stays within
  * the HBM budget; when the oldest waiting request does not fit the free budget, the first of
  * the next 15 that fits goes ahead of it, but no request is passed over more than 8 times.
- * Admission (host-to-device copy and initialisation) runs on its own
- * stream while the resident cases compute.  A case leaves after its step count, or early
- * when one of its sites becomes unstable.  Its result is bitwise the same whether it is
+ * Admission (an initialisation kernel that reads the request's fields in place from pinned,
+ * device-mapped host memory) runs on its own stream while the resident cases compute.  A case
+ * leaves after its step count, or early when one of its sites becomes unstable; its fields are
+ * then written back, again in place into pinned host memory, on a third stream while the
+ * next steps run.  Its result is bitwise the same whether it is
  * served alone or in any mix (sites are independent and every case runs the same kernel),
  * and equals lbm_step's to rounding (the same arithmetic, compiled into another kernel).
  * A scheduler thread owned by the server does all GPU work; the calls are thread-safe. */
@@ -287,15 +289,16 @@ typedef struct {
 } lbm_server_stats;
 
 /* Creates a server on the current device.  hbm_budget_bytes bounds the resident cases'
- * population memory (the server adds ~170 MB of staging of its own); 1 <= max_cases <= 1024. */
+ * population memory (the server adds about 5 KB of tables per case slot); 1 <= max_cases <= 1024. */
 lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server** out);
 
 /* Queues one case: configuration (storage FP32, FP16 or BF16 offsets, fp64_moments = 0,
  * the series equilibrium of App. B or the exact entropic equilibrium of Sec. III, BGK collision,
  * ping-pong streaming, x faces periodic, zero-gradient or equilibrium inflow; cuda_stream is
- * ignored), initial fields in host memory (layout as lbm_init; copied
- * before the call returns) and nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case
- * alone exceeds the budget, LBM_EINVAL for an invalid configuration. */
+ * ignored), initial fields in host memory (layout as lbm_init; copied into pinned host memory
+ * of the request's own, 80 bytes per site with its result, before the call returns) and
+ * nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case alone exceeds the budget or its
+ * pinned memory cannot be allocated, LBM_EINVAL for an invalid configuration. */
 lbm_status lbm_submit(lbm_server* srv, const lbm_config* cfg, const double* rho, const double* u,
                       const double* theta, long long nsteps, long long* ticket);
 

@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kMaxServerCases = 1024;
 constexpr int kTickSteps = 16;            // longest tick (steps between scheduler decisions)
-constexpr long long kXferChunk = 1LL << 21;  // sites per host transfer chunk
 // Admission is first fit in submission order over the oldest kAdmitLookahead waiting requests;
 // a request passed over kMaxBypass times holds back every later one until it is admitted.
 constexpr int kAdmitLookahead = 16;
@@ -188,18 +187,48 @@ __global__ void served_zero_gradient_kernel(const CaseDesc* __restrict__ cases, 
 
 using Clock = std::chrono::steady_clock;
 
+// Pinned, device-mapped host memory (a request's fields), freed with its owner.  The kernels read
+// and write it in place over the host link: no staging copy, nothing for the scheduler to wait on.
+struct HostFields {
+  double* p = nullptr;
+  HostFields() = default;
+  HostFields(const HostFields&) = delete;
+  HostFields& operator=(const HostFields&) = delete;
+  ~HostFields() {
+    if (p) cudaFreeHost(p);
+  }
+  bool alloc(long long n) {
+    void* q = nullptr;
+    if (cudaHostAlloc(&q, static_cast<size_t>(n) * sizeof(double), cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    p = static_cast<double*>(q);
+    return true;
+  }
+};
+
 struct Request {
   long long ticket = 0;
   lbm_config cfg{};
   long long nsteps = 0;
   long long sites = 0;
   size_t footprint = 0;
-  std::vector<double> in;   // rho | u (3 * sites) | theta
-  std::vector<double> out;  // same layout, filled at retirement
+  HostFields in;   // rho | u (3 * sites) | theta
+  HostFields out;  // same layout, written at retirement
   Clock::time_point t_submit, t_done;
   lbm_status status = LBM_EBUSY;
   bool done = false;
   int bypassed = 0;         // later requests admitted before this one
+};
+
+// A case whose fields are being read back (on the retire stream) and whose memory is being freed.
+struct Retiring {
+  std::shared_ptr<Request> req;
+  int slot = -1;
+  lbm_status status = LBM_OK;
+  cudaEvent_t done = nullptr;
 };
 
 struct Resident {
@@ -220,12 +249,14 @@ struct Resident {
 struct lbm_server {
   using Request = lbm::Request;
   using Resident = lbm::Resident;
+  using Retiring = lbm::Retiring;
 
   size_t budget = 0;
   int max_cases = 0;
   int device = 0;
   lbm::LatticeTables tab{};
-  cudaStream_t compute = nullptr, admit = nullptr;
+  cudaStream_t compute = nullptr, admit = nullptr, retire = nullptr;
+  cudaEvent_t tick_done = nullptr;
   lbm::CaseDesc* d_cases = nullptr;
   lbm::CaseDesc* h_cases = nullptr;  // pinned staging
   lbm::CaseSlabs* d_slabs = nullptr;  // per table position and parity (2 per case)
@@ -233,8 +264,6 @@ struct lbm_server {
   long long slabs_version = -1;       // membership version the device table was written for
   unsigned int* d_flags = nullptr;
   unsigned int* h_flags = nullptr;   // pinned
-  double* d_admit_scratch = nullptr;
-  double* d_retire_scratch = nullptr;
   int grid_blocks = 0;
 
   std::mutex mu;
@@ -242,6 +271,7 @@ struct lbm_server {
   std::deque<std::shared_ptr<Request>> queue;          // submitted, not admitted
   std::unordered_map<long long, std::shared_ptr<Request>> requests;
   std::vector<Resident> active, joining;
+  std::vector<Retiring> retiring;
   std::vector<int> free_slots;
   size_t resident_bytes = 0;
   long long next_ticket = 1;
@@ -290,21 +320,13 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
   const size_t bb = static_cast<size_t>(2 * res.g.sub_stride) * storage_bytes(r->cfg.storage);
   for (int b = 0; b < 2; ++b) SRV_CK(s, cudaMallocAsync(&res.buf[b], bb, s->admit));
   SRV_CK(s, cudaMemsetAsync(s->d_flags + slot, 0, sizeof(unsigned int), s->admit));
+  // the init kernel reads the request's pinned fields in place
   const long long S = r->sites;
-  double* sr = s->d_admit_scratch;
-  double* su = sr + kXferChunk;
-  double* st = su + 3 * kXferChunk;
-  for (long long first = 0; first < S; first += kXferChunk) {
-    const long long cnt = std::min(kXferChunk, S - first);
-    const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
-    SRV_CK(s, cudaMemcpyAsync(sr, r->in.data() + first, nb, cudaMemcpyHostToDevice, s->admit));
-    for (int a = 0; a < 3; ++a)
-      SRV_CK(s, cudaMemcpyAsync(su + a * cnt, r->in.data() + S + a * S + first, nb, cudaMemcpyHostToDevice, s->admit));
-    SRV_CK(s, cudaMemcpyAsync(st, r->in.data() + 4 * S + first, nb, cudaMemcpyHostToDevice, s->admit));
-    SRV_CK(s, launch_init(r->cfg.storage, r->cfg.equilibrium, res.g, s->tab, res.buf[0], sr, su, st, first, cnt, cnt,
-                          s->admit, s->d_flags + slot));
-    ++s->stats.kernel_launches;
-  }
+  double* din = nullptr;
+  SRV_CK(s, cudaHostGetDevicePointer(reinterpret_cast<void**>(&din), r->in.p, 0));
+  SRV_CK(s, launch_init(r->cfg.storage, r->cfg.equilibrium, res.g, s->tab, res.buf[0], din, din + S, din + 4 * S, 0, S,
+                        S, s->admit, s->d_flags + slot));
+  ++s->stats.kernel_launches;
   for (int face = 0; face < 2; ++face) {
     const lbm_bc& b = r->cfg.face[face];
     if (b.kind != LBM_BC_EQ_INFLOW) continue;
@@ -320,16 +342,18 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
   }
   SRV_CK(s, cudaEventCreateWithFlags(&res.ready, cudaEventDisableTiming));
   SRV_CK(s, cudaEventRecord(res.ready, s->admit));
-  // the admission stream reuses its scratch only after this case's copies are done
-  SRV_CK(s, cudaStreamSynchronize(s->admit));
   s->joining.push_back(res);
   return LBM_OK;
 }
+
+lbm_status finish_retirements(lbm_server* s);
 
 // Admits queued requests while a slot is free: the first of the oldest kAdmitLookahead that fits
 // the remaining budget, so that one large request at the head does not leave the budget idle;
 // a request passed over kMaxBypass times is admitted before any later one.
 lbm_status admit_some(lbm_server* s) {
+  const lbm_status fr = finish_retirements(s);
+  if (fr != LBM_OK) return fr;
   for (;;) {
     std::shared_ptr<Request> r;
     int slot = -1;
@@ -398,42 +422,60 @@ void drop_graphs(lbm_server* s) {
   s->graphs.clear();
 }
 
-// Copies a retiring case's fields to its request and releases its memory.
-lbm_status retire(lbm_server* s, Resident& res, lbm_status status) {
+// Starts a case's retirement on the retire stream, after the tick that finished it: the moments
+// kernel writes its fields into the request's pinned output in place, then its buffers are freed.
+// The scheduler goes on with the next tick; finish_retirements completes the request.
+lbm_status begin_retire(lbm_server* s, Resident& res, lbm_status status) {
   Request& r = *res.req;
   const long long S = r.sites;
-  r.out.assign(static_cast<size_t>(5 * S), 0.0);
-  double* sr = s->d_retire_scratch;
-  double* su = sr + kXferChunk;
-  double* st = su + 3 * kXferChunk;
-  for (long long first = 0; first < S; first += kXferChunk) {
-    const long long cnt = std::min(kXferChunk, S - first);
-    const size_t nb = static_cast<size_t>(cnt) * sizeof(double);
-    SRV_CK(s, launch_moments(r.cfg.storage, res.g, s->tab, res.buf[res.parity], sr, su, st, first, cnt, cnt,
-                             s->compute));
-    ++s->stats.kernel_launches;
-    SRV_CK(s, cudaMemcpyAsync(r.out.data() + first, sr, nb, cudaMemcpyDeviceToHost, s->compute));
-    for (int a = 0; a < 3; ++a)
-      SRV_CK(s, cudaMemcpyAsync(r.out.data() + S + a * S + first, su + a * cnt, nb, cudaMemcpyDeviceToHost,
-                                s->compute));
-    SRV_CK(s, cudaMemcpyAsync(r.out.data() + 4 * S + first, st, nb, cudaMemcpyDeviceToHost, s->compute));
-  }
-  for (int b = 0; b < 2; ++b) SRV_CK(s, cudaFreeAsync(res.buf[b], s->compute));
-  SRV_CK(s, cudaStreamSynchronize(s->compute));
+  double* dout = nullptr;
+  SRV_CK(s, cudaHostGetDevicePointer(reinterpret_cast<void**>(&dout), r.out.p, 0));
+  SRV_CK(s, cudaStreamWaitEvent(s->retire, s->tick_done, 0));
+  SRV_CK(s, launch_moments(r.cfg.storage, res.g, s->tab, res.buf[res.parity], dout, dout + S, dout + 4 * S, 0, S, S,
+                           s->retire));
+  for (int b = 0; b < 2; ++b) SRV_CK(s, cudaFreeAsync(res.buf[b], s->retire));
+  Retiring rt;
+  rt.req = res.req;
+  rt.slot = res.slot;
+  rt.status = status;
+  SRV_CK(s, cudaEventCreateWithFlags(&rt.done, cudaEventDisableTiming));
+  SRV_CK(s, cudaEventRecord(rt.done, s->retire));
   if (res.ready) cudaEventDestroy(res.ready);
+  s->retiring.push_back(rt);
   std::lock_guard<std::mutex> lk(s->mu);
-  r.t_done = Clock::now();
-  r.status = status;
-  r.done = true;
-  r.in.clear();
-  r.in.shrink_to_fit();
-  s->resident_bytes -= r.footprint;
-  s->free_slots.push_back(res.slot);
-  ++s->stats.completed;
-  if (status == LBM_EUNSTABLE) ++s->stats.unstable;
-  else s->stats.site_updates += S * r.nsteps;
-  s->cv_done.notify_all();
-  s->cv_work.notify_all();
+  ++s->stats.kernel_launches;
+  return LBM_OK;
+}
+
+// Completes the retirements whose read-back has finished: the request is done, its footprint and
+// slot return to the pool.
+lbm_status finish_retirements(lbm_server* s) {
+  for (size_t k = 0; k < s->retiring.size();) {
+    Retiring& rt = s->retiring[k];
+    const cudaError_t e = cudaEventQuery(rt.done);
+    if (e == cudaErrorNotReady) {
+      ++k;
+      continue;
+    }
+    if (e != cudaSuccess) return set_fatal(s, std::string("retirement failed: ") + cudaGetErrorString(e));
+    cudaEventDestroy(rt.done);
+    // the scheduler drops its reference before the request shows as done, so that the client's
+    // poll releases the pinned fields on its own thread
+    std::lock_guard<std::mutex> lk(s->mu);
+    Request& r = *rt.req;
+    r.t_done = Clock::now();
+    r.status = rt.status;
+    s->resident_bytes -= r.footprint;
+    s->free_slots.push_back(rt.slot);
+    ++s->stats.completed;
+    if (rt.status == LBM_EUNSTABLE) ++s->stats.unstable;
+    else s->stats.site_updates += r.sites * r.nsteps;
+    r.done = true;
+    s->retiring[k] = std::move(s->retiring.back());
+    s->retiring.pop_back();
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
   return LBM_OK;
 }
 
@@ -510,6 +552,7 @@ lbm_status run_tick(lbm_server* s) {
   cudaGraphExec_t g = tick_graph(s, ncases, plan, total_rows, K);
   if (!g) return set_fatal(s, "CUDA graph capture of a serving tick failed");
   SRV_CK(s, cudaGraphLaunch(g, s->compute));
+  SRV_CK(s, cudaEventRecord(s->tick_done, s->compute));
   ++s->stats.graph_launches;
   int groups = 0;
   for (int gi = 0; gi < kGroups; ++gi) groups += plan.count[gi] > 0;
@@ -527,7 +570,7 @@ lbm_status run_tick(lbm_server* s) {
     a.parity ^= (K & 1);
     const bool unstable = s->h_flags[a.slot] != 0;
     if (a.steps_left == 0 || unstable) {
-      st = retire(s, a, unstable ? LBM_EUNSTABLE : LBM_OK);
+      st = begin_retire(s, a, unstable ? LBM_EUNSTABLE : LBM_OK);
       if (st != LBM_OK) return st;
     } else {
       keep.push_back(a);
@@ -548,11 +591,11 @@ void worker_main(lbm_server* s) {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop || s->fatal != LBM_OK) break;
       if (s->active.empty() && s->joining.empty() && s->queue.empty())
-        s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(s->retiring.empty() ? 20 : 1));
       if (s->stop) break;
     }
     if (admit_some(s) != LBM_OK) break;
-    if (s->active.empty() && s->joining.empty()) continue;
+    if (s->active.empty() && s->joining.empty()) continue;  // (admit_some also finished retirements)
     const auto t0 = Clock::now();
     size_t held = 0;
     bool backlog = false;  // requests waiting for admission when the tick starts
@@ -602,16 +645,16 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
   };
   if (cudaGetDevice(&s->device) != cudaSuccess) return bail("cudaGetDevice failed");
   if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->retire, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->tick_done, cudaEventDisableTiming) != cudaSuccess)
     return bail("stream creation failed");
   if (cudaMalloc(&s->d_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
       cudaMallocHost(&s->h_cases, sizeof(CaseDesc) * max_cases) != cudaSuccess ||
       cudaMalloc(&s->d_slabs, sizeof(CaseSlabs) * 2 * max_cases) != cudaSuccess ||
       cudaMallocHost(&s->h_slabs, sizeof(CaseSlabs) * 2 * max_cases) != cudaSuccess ||
       cudaMalloc(&s->d_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
-      cudaMallocHost(&s->h_flags, sizeof(unsigned int) * max_cases) != cudaSuccess ||
-      cudaMalloc(&s->d_admit_scratch, 5 * kXferChunk * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&s->d_retire_scratch, 5 * kXferChunk * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&s->h_flags, sizeof(unsigned int) * max_cases) != cudaSuccess) {
     cudaGetLastError();
     return bail("device allocation failed");
   }
@@ -661,10 +704,14 @@ lbm_status lbm_submit(lbm_server* s, const lbm_config* cfg, const double* rho, c
     return LBM_ENOMEM;
   }
   const long long S = r->sites;
-  r->in.resize(static_cast<size_t>(5 * S));
-  std::memcpy(r->in.data(), rho, S * sizeof(double));
-  std::memcpy(r->in.data() + S, u, 3 * S * sizeof(double));
-  std::memcpy(r->in.data() + 4 * S, theta, S * sizeof(double));
+  if (!r->in.alloc(5 * S) || !r->out.alloc(5 * S)) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->err = "pinned host memory for the request's fields could not be allocated";
+    return LBM_ENOMEM;
+  }
+  std::memcpy(r->in.p, rho, S * sizeof(double));
+  std::memcpy(r->in.p + S, u, 3 * S * sizeof(double));
+  std::memcpy(r->in.p + 4 * S, theta, S * sizeof(double));
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -692,9 +739,9 @@ lbm_status lbm_poll(lbm_server* s, long long ticket, double* rho, double* u, dou
     s->requests.erase(it);
   }
   const long long S = r->sites;
-  if (rho) std::memcpy(rho, r->out.data(), S * sizeof(double));
-  if (u) std::memcpy(u, r->out.data() + S, 3 * S * sizeof(double));
-  if (theta) std::memcpy(theta, r->out.data() + 4 * S, S * sizeof(double));
+  if (rho) std::memcpy(rho, r->out.p, S * sizeof(double));
+  if (u) std::memcpy(u, r->out.p + S, 3 * S * sizeof(double));
+  if (theta) std::memcpy(theta, r->out.p + 4 * S, S * sizeof(double));
   if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
   return r->status;
 }
@@ -740,6 +787,10 @@ lbm_status lbm_server_destroy(lbm_server* s) {
   if (prev != s->device) cudaSetDevice(s->device);
   if (s->compute) cudaStreamSynchronize(s->compute);
   if (s->admit) cudaStreamSynchronize(s->admit);
+  if (s->retire) cudaStreamSynchronize(s->retire);
+  for (auto& rt : s->retiring)
+    if (rt.done) cudaEventDestroy(rt.done);
+  s->retiring.clear();
   for (auto* v : {&s->active, &s->joining})
     for (auto& a : *v) {
       for (int b = 0; b < 2; ++b)
@@ -753,10 +804,10 @@ lbm_status lbm_server_destroy(lbm_server* s) {
   if (s->h_slabs) cudaFreeHost(s->h_slabs);
   if (s->d_flags) cudaFree(s->d_flags);
   if (s->h_flags) cudaFreeHost(s->h_flags);
-  if (s->d_admit_scratch) cudaFree(s->d_admit_scratch);
-  if (s->d_retire_scratch) cudaFree(s->d_retire_scratch);
+  if (s->tick_done) cudaEventDestroy(s->tick_done);
   if (s->compute) cudaStreamDestroy(s->compute);
   if (s->admit) cudaStreamDestroy(s->admit);
+  if (s->retire) cudaStreamDestroy(s->retire);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   delete s;
   return LBM_OK;
