@@ -263,12 +263,21 @@ __device__ __forceinline__ float log1p_alpha(float y) {
 }
 __device__ __forceinline__ double log1p_alpha(double y) { return log1p(y); }
 
-// The full-expression solve.  The walk runs once, to collect x_i and w_i F_i per thread; the
-// sums over directions are then short runtime loops (an unrolled evaluation per iterate would
-// not fit the instruction cache).  FP32 keeps the 2 x 81 values in dynamic shared memory, one
-// column per thread ([2][81][blockDim.x]: consecutive threads, consecutive banks), 648 bytes a
-// thread: in per-thread local memory they overflowed L1 at any useful occupancy and every pass
-// went to L2 (1274 DRAM bytes a site against 648).  FP64 keeps a local array.
+// Per-thread columns of x_i and w_i F_i for the alpha solve.  The walk over the directions runs
+// once, to fill them; the sums over directions are then short runtime loops (an unrolled
+// evaluation per iterate would not fit the instruction cache).  FP32 keeps the 2 x 81 values
+// in dynamic shared memory, one column per thread ([2][81][blockDim.x]: consecutive threads,
+// consecutive banks), 648 bytes a thread: in per-thread local memory they overflowed L1 at any
+// useful occupancy and every pass went to L2 (1274 DRAM bytes a site against 648).  FP64 keeps
+// a local array.
+template <class R>
+struct AlphaColumns {
+  R* xs;
+  R* wf;
+  int stride;
+};
+
+// The full-expression solve on the columns.
 // Each pass expands Delta H about a centre a0 exactly in delta = alpha - a0: with u_i = 1 + a0 x_i,
 // L_i = log u_i and z_i = x_i / u_i,
 //   Delta H(a0 + delta) = F0 + F1 delta + sum_{n>=2} (-1)^n M_n delta^n / (n (n-1)),
@@ -279,50 +288,43 @@ __device__ __forceinline__ double log1p_alpha(double y) { return log1p(y); }
 // by the slope F1), or when delta itself is below it; otherwise the root becomes the next centre,
 // kept inside the bracket [lo, hi] that the signs of F0 maintain (bisection when it would leave
 // it).  One pass usually suffices: populations with large |z| weigh little in the bound.
-template <class Store, class R>
-__device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho, const LatticeTables& tb, R amax) {
+// The test for a root before alpha_max (Delta H(alpha_max) <= 0: alpha = alpha_max) takes one
+// more logarithm per population.  It runs with the first pass when alpha_max < 5/2 (near the
+// usual root, where it often decides), and otherwise only once a root estimate reaches
+// alpha_max: a root found below alpha_max already implies Delta H(alpha_max) > 0, since Delta H
+// is convex, zero at 0 and negative at 1.  The direction loops are unrolled by 3 (81 = 3 x 27)
+// so that three populations' dependent chains interleave.
+template <class R>
+__device__ __forceinline__ R entropic_alpha_full(const AlphaColumns<R>& c, R amax) {
   constexpr bool kDbl = std::is_same_v<R, double>;
   constexpr int N = kDbl ? 10 : 6;
   constexpr int kMaxPass = kDbl ? 40 : 20;
   const R tol = R(kDbl ? 1e-14 : 1e-6);
-  [[maybe_unused]] R xs_local[kDbl ? kQ : 1], wf_local[kDbl ? kQ : 1];
-  R* xs;
-  R* wf;
-  int stride;
-  if constexpr (kDbl) {
-    xs = xs_local;
-    wf = wf_local;
-    stride = 1;
-  } else {
-    extern __shared__ float alpha_smem[];
-    xs = alpha_smem + threadIdx.x;
-    wf = alpha_smem + kQ * blockDim.x + threadIdx.x;
-    stride = blockDim.x;
-  }
-  int n = 0;
-  visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
-    xs[n * stride] = ratio(E - F, F);
-    wf[n * stride] = wg * F;
-    ++n;
-  });
+  const R* xs = c.xs;
+  const R* wf = c.wf;
+  const int stride = c.stride;
+  const bool finite = amax < R(1e30);
+  const bool eager = amax < R(2.5);
+  // Delta H(alpha_max) + alpha_max b (the limiting population's term is 1 there)
+  auto dh_amax = [&]() {
+    R Sm = R(0);
+#pragma unroll 3
+    for (int i = 0; i < kQ; ++i) {
+      const R x = xs[i * stride], w = wf[i * stride];
+      const R ym = amax * x;
+      Sm += w * (ym > R(-1) ? (R(1) + ym) * log1p_alpha(ym) - ym : R(1));
+    }
+    return Sm;
+  };
   R lo = R(1), hi = amax;
   R a0 = fmin(R(2), R(1) + R(0.9) * (amax - R(1)));
   R b = R(0);
+  bool checked = false;
   for (int pass = 0; pass < kMaxPass; ++pass) {
-    // the first pass also sums b = <f, x log(1 + x)> and Delta H(alpha_max) (the limiting
-    // population's term is 1 there)
-    R Sm = R(0);
     R F0 = R(0), F1 = R(0), zmax = R(0), Mabs = R(0), M[N - 1];  // M[k] = M_{k+2}
 #pragma unroll
     for (int k = 0; k < N - 1; ++k) M[k] = R(0);
-#pragma unroll 1
-    for (int i = 0; i < kQ; ++i) {
-      const R x = xs[i * stride], w = wf[i * stride];
-      if (pass == 0) {
-        const R ym = amax * x;
-        b += w * x * log1p_alpha(x);
-        Sm += w * (ym > R(-1) ? (R(1) + ym) * log1p_alpha(ym) - ym : R(1));
-      }
+    auto term = [&](R x, R w) {
       const R y = a0 * x, u = R(1) + y;
       const R L = log1p_alpha(y);
       const R z = ratio(x, u);
@@ -336,8 +338,28 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
         M[k] += t;
       }
       Mabs += fabs(t * z);
+    };
+    if (pass == 0) {
+      // the first pass also sums b = <f, x log(1 + x)>, and Delta H(alpha_max) when eager
+      R Sm = R(0);
+#pragma unroll 3
+      for (int i = 0; i < kQ; ++i) {
+        const R x = xs[i * stride], w = wf[i * stride];
+        b += w * x * log1p_alpha(x);
+        if (eager) {
+          const R ym = amax * x;
+          Sm += w * (ym > R(-1) ? (R(1) + ym) * log1p_alpha(ym) - ym : R(1));
+        }
+        term(x, w);
+      }
+      if (eager && finite) {
+        checked = true;
+        if (Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
+      }
+    } else {
+#pragma unroll 3
+      for (int i = 0; i < kQ; ++i) term(xs[i * stride], wf[i * stride]);
     }
-    if (pass == 0 && amax < R(1e30) && Sm - amax * b <= R(0)) return amax;  // no root before the positivity boundary
     F0 -= a0 * b;
     F1 -= b;
     if (F0 < R(0)) lo = a0; else hi = a0;
@@ -348,16 +370,20 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
 #pragma unroll
       for (int k = 0; k < N - 1; ++k) {
         const int nn = k + 2;
-        const R c = ((nn % 2 == 0) ? R(1) : R(-1)) * M[k];
-        dG += c * p * R(1.0 / (nn - 1));
+        const R cf = ((nn % 2 == 0) ? R(1) : R(-1)) * M[k];
+        dG += cf * p * R(1.0 / (nn - 1));
         p *= d;
-        G += c * p * R(1.0 / (nn * (nn - 1)));
+        G += cf * p * R(1.0 / (nn * (nn - 1)));
       }
       const R step = G / dG;
       d -= step;
       if (!(fabs(step) > tol * a0)) break;
     }
     const R na = a0 + d;
+    if (!checked && finite && !(na < hi)) {
+      checked = true;
+      if (dh_amax() - amax * b <= R(0)) return amax;
+    }
     const R q = fabs(d) * zmax;
     R bound = R(1e30);
     if (q < R(1)) {
@@ -373,45 +399,66 @@ __device__ __forceinline__ R entropic_alpha_full(const R* f, const R* lam, R rho
   return a0;
 }
 
+// One walk over the populations fills the columns (x_i = feq_i / f_i - 1 and w_i F_i) and
+// finds min x, max |x| and min F; then the series form when every |x_i| <= kX (its moments
+// a_n = <f, x^n> summed from the columns), else the full expression.
 template <class Store, class R>
 __device__ __forceinline__ R entropic_alpha(const R* f, const R* lam, R rho, const LatticeTables& tb) {
   constexpr bool kDbl = std::is_same_v<R, double>;
   constexpr int N = kDbl ? 8 : 6;
   const R kX = R(kDbl ? 0.01 : 0.05);
-  R an[N - 1];  // a_2 .. a_N
-#pragma unroll
-  for (int k = 0; k < N - 1; ++k) an[k] = R(0);
+  [[maybe_unused]] R xs_local[kDbl ? kQ : 1], wf_local[kDbl ? kQ : 1];
+  AlphaColumns<R> c;
+  if constexpr (kDbl) {
+    c = AlphaColumns<R>{xs_local, wf_local, 1};
+  } else {
+    extern __shared__ float alpha_smem[];
+    c = AlphaColumns<R>{alpha_smem + threadIdx.x, alpha_smem + kQ * blockDim.x + threadIdx.x,
+                        static_cast<int>(blockDim.x)};
+  }
   R xmin = R(0), xabs = R(0), Fmin = R(1);
+  int n = 0;
   visit_populations<Store>(f, lam, rho, tb, [&](R F, R E, R wg) {
     const R x = ratio(E - F, F);
     Fmin = fmin(Fmin, F);
     xmin = fmin(xmin, x);
     xabs = fmax(xabs, fabs(x));
-    R pw = wg * F * x;
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k) {
-      pw *= x;
-      an[k] += pw;
-    }
+    c.xs[n * c.stride] = x;
+    c.wf[n * c.stride] = wg * F;
+    ++n;
   });
-  if (!(Fmin > R(0)) || !(an[0] > R(0))) return R(2);
+  if (!(Fmin > R(0)) || !(xabs > R(0))) return R(2);
   R al = R(2);
   if (xabs <= kX) {
+    R an[N - 1];  // a_2 .. a_N
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) an[k] = R(0);
+#pragma unroll 3
+    for (int i = 0; i < kQ; ++i) {
+      const R x = c.xs[i * c.stride];
+      R pw = c.wf[i * c.stride] * x;
+#pragma unroll
+      for (int k = 0; k < N - 1; ++k) {
+        pw *= x;
+        an[k] += pw;
+      }
+    }
+    if (!(an[0] > R(0))) return R(2);
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
       R G = R(0), dG = R(0), pw = R(1);  // pw = al^(n-2)
 #pragma unroll
       for (int k = 0; k < N - 1; ++k) {
-        const int n = k + 2;
-        const R sa = (n % 2 == 0) ? an[k] : -an[k];
-        G += sa * (pw * al * R(1.0 / (n * (n - 1))) - R(1.0 / (n - 1)));
-        dG += sa * pw * R(1.0 / n);
+        const int nn = k + 2;
+        const R sa = (nn % 2 == 0) ? an[k] : -an[k];
+        G += sa * (pw * al * R(1.0 / (nn * (nn - 1))) - R(1.0 / (nn - 1)));
+        dG += sa * pw * R(1.0 / nn);
         pw *= al;
       }
       al -= G / dG;
     }
   } else {
-    al = entropic_alpha_full<Store>(f, lam, rho, tb, xmin < R(0) ? R(-1) / xmin : R(1e30));
+    al = entropic_alpha_full<R>(c, xmin < R(0) ? R(-1) / xmin : R(1e30));
   }
   return (al > R(0) && al < R(1e30)) ? al : R(2);
 }
