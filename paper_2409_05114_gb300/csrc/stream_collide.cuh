@@ -88,36 +88,70 @@ struct Moments {
 // <f, c^2> = 3 theta0 + <w, d c^2> (the weights' own moments are 1, 0, 3 theta0).
 // FP32 sums of FP32 populations are also taken over the deviations f_i - w_i: the same
 // moments, summed from numbers ~10x smaller than f_i, hence ~10x smaller rounding.
-// FP32 storage with FP64-quality moments: cascaded sums (Sum2 and Dot2 of Ogita, Rump and
-// Oishi) of the 81 stored values.  The running sums stay floats; the rounding error of every
-// addition (TwoSum) and product (TwoProd) collects in a second float, which is as accurate as
-// summing in twice the working precision -- about 2^-48, against 2^-53 for FP64, at FP32 rates
-// (this GPU runs FP64 at 1/64 of them).  c^2 and c_a / 2 are exact floats.
+// FP32 storage with FP64-quality moments: exact integer sums.  With h_i = 2 c_i (integers) the
+// moments are rho = <f, 1>, j_a = <f, h_a> / 2 and <f, c^2> = <f, h^2> / 4.  Every population is
+// scaled by 2^K (exact) and rounded to a 64-bit integer, an error below 2^-(K+1) in f; the
+// integer sums are then exact.  K is the largest exponent with B 2^K < 2^61, B = sum_i |f_i|
+// (1 + h_i^2) (taken in FP32 with a margin), so that no partial sum of the rho, h_a or h^2
+// weighted integers can leave (-2^62, 2^62).  The roundings add at most 81 2^-(K+1) < 2^-54 B to
+// rho and sum_i h_i^2 2^-(K+1) < 2^-49 B to <f, h^2> -- with B about 6 rho near theta0, the
+// FP64 level (K is capped at 120, which costs relative precision only below B ~ 2^-59).  Each
+// shell's populations (pair sums and differences) are added first and weighted by the shell's
+// h^2 and |h_a| once.  The sums return as double words (the rounded integer and its
+// remainder, each converted once), scaled back exactly.  A non-finite population makes the
+// moments NaN, which the caller flags.
+__device__ __forceinline__ Dw fixed_to_dw(long long m, float scale) {
+  const float hi = __ll2float_rn(m);
+  const float lo = __ll2float_rn(m - __float2ll_rn(hi));
+  return Dw{hi * scale, lo * scale};
+}
+
 __device__ __forceinline__ Moments<Dw> site_moments_dw(const float* f) {
-  float pr = f[0], qr = 0.0f, pe = 0.0f, qe = 0.0f, px = 0.0f, qx = 0.0f, py = 0.0f, qy = 0.0f, pz = 0.0f,
-        qz = 0.0f;
-  // p + q += a (v.hi + v.lo), a exact
-  auto acc = [](float& p, float& q, float a, Dw v) {
-    const Dw h = two_prod(a, v.hi);
-    const Dw t = two_sum(p, h.hi);
-    p = t.hi;
-    q = __fadd_rn(q, __fadd_rn(t.lo, __fmaf_rn(a, v.lo, h.lo)));
-  };
+  float B = fabsf(f[0]);
+  static_for<kPairs>([&](auto Pc) {
+    constexpr int P = decltype(Pc)::value;
+    constexpr float g = 1.0f + static_cast<float>(4.0 * rd3q81::kShellC2[rd3q81::kDirs[1 + 2 * P].shell]);
+    B = fmaf(fabsf(f[1 + 2 * P]) + fabsf(f[2 + 2 * P]), g, B);
+  });
+  // 2^e > B (1 + 2^-10) covers the FP32 rounding of B (below 2^-17 relative)
+  const int e = ((__float_as_int(B * 1.0009765625f) >> 23) & 0xff) - 126;
+  const int K = min(61 - e, 120);
+  const float sc = __int_as_float((K + 127) << 23);
+  // two's-complement sums in unsigned arithmetic (wrapping defined even for a non-finite input)
+  using U = unsigned long long;
+  U rho = static_cast<U>(__float2ll_rn(f[0] * sc)), e2 = 0, jx = 0, jy = 0, jz = 0;
+  U S = 0, X = 0, Y = 0, Z = 0;
   static_for<kPairs>([&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
     constexpr rd3q81::Dir d = rd3q81::kDirs[1 + 2 * P];
-    constexpr float c2 = static_cast<float>(rd3q81::kShellC2[d.shell]);
-    const float fp = f[1 + 2 * P], fm = f[2 + 2 * P];
-    const Dw sum = two_sum(fp, fm), dif = two_sum(fp, -fm);
-    const Dw t = two_sum(pr, sum.hi);
-    pr = t.hi;
-    qr = __fadd_rn(qr, __fadd_rn(t.lo, sum.lo));
-    acc(pe, qe, c2, sum);
-    if constexpr (d.hx != 0) acc(px, qx, 0.5f * d.hx, dif);
-    if constexpr (d.hy != 0) acc(py, qy, 0.5f * d.hy, dif);
-    if constexpr (d.hz != 0) acc(pz, qz, 0.5f * d.hz, dif);
+    constexpr int s = d.shell;
+    constexpr bool first = P == 0 || rd3q81::kDirs[2 * P - 1].shell != s;
+    constexpr bool last = P == kPairs - 1 || rd3q81::kDirs[3 + 2 * P].shell != s;
+    const U ip = static_cast<U>(__float2ll_rn(f[1 + 2 * P] * sc)), im = static_cast<U>(__float2ll_rn(f[2 + 2 * P] * sc));
+    const U sum = ip + im, dif = ip - im;
+    if constexpr (first) S = X = Y = Z = 0;
+    S += sum;
+    if constexpr (d.hx != 0) X = d.hx > 0 ? X + dif : X - dif;
+    if constexpr (d.hy != 0) Y = d.hy > 0 ? Y + dif : Y - dif;
+    if constexpr (d.hz != 0) Z = d.hz > 0 ? Z + dif : Z - dif;
+    // (empty) ordering point: without it the compiler converts all 81 populations up front and
+    // holds 162 registers of integers
+    asm volatile("" : "+l"(S), "+l"(X), "+l"(Y), "+l"(Z));
+    if constexpr (last) {
+      constexpr U h2 = static_cast<U>(4.0 * rd3q81::kShellC2[s] + 0.5);
+      constexpr U k = static_cast<U>(rd3q81::shell_shape(s).k);
+      rho += S;
+      e2 += h2 * S;
+      jx += k * X;
+      jy += k * Y;
+      jz += k * Z;
+    }
   });
-  return Moments<Dw>{fast_two_sum(pr, qr), two_sum(px, qx), two_sum(py, qy), two_sum(pz, qz), fast_two_sum(pe, qe)};
+  const bool ok = B <= FLT_MAX;
+  const float s0 = ok ? __int_as_float((127 - K) << 23) : __int_as_float(0x7fc00000);
+  const float s1 = 0.5f * s0, s2 = 0.25f * s0;
+  auto dw = [](U m, float scale) { return fixed_to_dw(static_cast<long long>(m), scale); };
+  return Moments<Dw>{dw(rho, s0), dw(jx, s1), dw(jy, s1), dw(jz, s1), dw(e2, s2)};
 }
 
 // Offset storage with FP64-quality moments: rho = 1 + sum_s w_s S_s, <f, c^2> = 3 theta0 + sum_s
@@ -252,14 +286,16 @@ __device__ __forceinline__ void visit_populations(const R* f, const R* lam, R rh
 // log(1 + y) for y > -1, FP32: for |y| < 1/4 from log(1 + y) = 2 atanh(s), s = y / (2 + y)
 // (|s| <= 1/7; the odd series to s^9 leaves below 1e-9 relative); otherwise the hardware
 // logarithm of u = 1 + y, corrected for the rounding of u by (y - (u - 1)) / u.  Relative error
-// below 2e-6 everywhere (the hardware log2 is good to 2^-21 absolute on [1/2, 2]).
+// below 2e-6 everywhere (the hardware log2 is good to 2^-21 absolute on [1/2, 2]).  Both forms
+// are evaluated and one is selected: a branch would split the unrolled direction loops of the
+// alpha solve into blocks the compiler cannot interleave (measured 7 % slower for FP32 storage,
+// 23 % for FP16).
 __device__ __forceinline__ float log1p_alpha(float y) {
   const float u = 1.0f + y;
-  if (fabsf(y) < 0.25f) {
-    const float s = __fdividef(y, 2.0f + y), s2 = s * s;
-    return 2.0f * s * (1.0f + s2 * (1.0f / 3.0f + s2 * (0.2f + s2 * (1.0f / 7.0f + s2 * (1.0f / 9.0f)))));
-  }
-  return __logf(u) + __fdividef(y - (u - 1.0f), u);
+  const float s = __fdividef(y, 2.0f + y), s2 = s * s;
+  const float ser = 2.0f * s * (1.0f + s2 * (1.0f / 3.0f + s2 * (0.2f + s2 * (1.0f / 7.0f + s2 * (1.0f / 9.0f)))));
+  const float hw = __logf(u) + __fdividef(y - (u - 1.0f), u);
+  return fabsf(y) < 0.25f ? ser : hw;
 }
 __device__ __forceinline__ double log1p_alpha(double y) { return log1p(y); }
 
