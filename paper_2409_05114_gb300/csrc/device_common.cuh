@@ -479,11 +479,14 @@ __host__ __device__ __forceinline__ bool solve_spd5(const R* Jp, R* x) {
 // 16 it stays within 5e-6 of the FP64 run.  Converged sites exit early, so the cap costs the
 // others nothing.
 // On return lam holds multipliers whose moments are within tol of T (relative to rho for mass
-// and momentum, to <f, c^2> for energy), or the last iterate after max_it evaluations.
+// and momentum, to <f, c^2> for energy), or the last iterate after max_it evaluations, and Jout
+// (if given; element k at Jout[k * jstride]) the 15 entries of <f, phi phi^T> at lam (the last
+// evaluation).
 // Returns false if the iteration broke down (non-positive pivot or non-finite values).
 template <class R>
 __host__ __device__ __forceinline__ bool entropic_multipliers(const R* T, R ux, R uy, R uz, R theta, R tol,
-                                                              int max_it, const LatticeTables& tb, R* lam) {
+                                                              int max_it, const LatticeTables& tb, R* lam,
+                                                              R* Jout = nullptr, int jstride = 1) {
   const R q = ux * ux + uy * uy + uz * uz;
   const R t0 = R(rd3q81::kTheta0);
   lam[0] = R(-1.5) * elog(theta / t0) - q / (R(2) * theta);
@@ -498,8 +501,16 @@ __host__ __device__ __forceinline__ bool entropic_multipliers(const R* T, R ux, 
     R r[5] = {T[0] - J[0], T[1] - J[1], T[2] - J[2], T[3] - J[3], T[4] - J[4]};
     const bool small = fabs(r[0]) <= tol * T[0] && fabs(r[1]) <= tol * T[0] && fabs(r[2]) <= tol * T[0] &&
                        fabs(r[3]) <= tol * T[0] && fabs(r[4]) <= tol * T[4];
-    if (small || it + 1 >= max_it) return small || (J[0] == J[0]);
-    if (!solve_spd5<R>(J, r)) return false;
+    if (small || it + 1 >= max_it) {
+      if (Jout)
+        for (int k = 0; k < 15; ++k) Jout[k * jstride] = J[k];
+      return small || (J[0] == J[0]);
+    }
+    if (!solve_spd5<R>(J, r)) {
+      if (Jout)
+        for (int k = 0; k < 15; ++k) Jout[k * jstride] = J[k];
+      return false;
+    }
     for (int k = 0; k < 5; ++k) lam[k] += r[k];
   }
 }
