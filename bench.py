@@ -161,12 +161,13 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "bgk", streaming: str = "pingpong"):
+def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "bgk", streaming: str = "pingpong",
+                fp64_moments: bool = False):
     """DRAM bytes (read + write) of one fused-kernel launch, from the committed ncu record
     (bytes per site measured on a smaller grid, scaled by the sites; keyed by storage, plus
     "_entropic" for the exact-equilibrium kernel, "_elbm" for it with the entropic alpha and
-    "_exactw" for the series equilibrium with exact temperature weights, then "_aa" for in-place
-    streaming);
+    "_exactw" for the series equilibrium with exact temperature weights, then "_fp64m" for
+    FP64-quality moments and "_aa" for in-place streaming);
     None if the record is missing or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
@@ -175,7 +176,8 @@ def ncu_traffic(storage: str, sites: int, eq: str = "series", collision: str = "
     if rec.get("source_sha256") != kernel_source_sha():
         return None
     suffix = ("_elbm" if collision == "entropic" else "_entropic" if eq == "entropic"
-              else "_exactw" if eq == "series_exact_w" else "") + ("_aa" if streaming == "aa" else "")
+              else "_exactw" if eq == "series_exact_w" else "") + ("_fp64m" if fp64_moments else "") + \
+        ("_aa" if streaming == "aa" else "")
     k = rec.get("kernels", {}).get(storage + suffix)
     return None if k is None else int(round(k["dram_bytes_per_site"] * sites))
 
@@ -716,7 +718,7 @@ def ours(args):
                    "l2": "inputs larger than L2 (one step moves %.0f GB)" % (head["bytes_per_site"] * head["sites"] / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.storage, head["sites"], args.equilibrium, args.collision,
-                                                                 args.streaming),
+                                                                 args.streaming, args.fp64_moments),
                      "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
                      "bytes_per_site": head["bytes_per_site"]},
         "gpu_launches": head["launches"],
