@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--collision", default="bgk", choices=["bgk", "entropic"],
                    help="for --quick runs: BGK (alpha = 2) or the entropic alpha (needs --equilibrium entropic)")
     p.add_argument("--fp64-moments", action="store_true",
-                   help="for --quick runs: FP64-quality (double-word) moment sums and temperature recovery")
+                   help="for --quick runs: FP64-quality moment sums and temperature recovery")
     p.add_argument("--quick", action="store_true", help="headline only (no variants, e2e, CPU baseline)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-only", type=int, default=0, metavar="K",

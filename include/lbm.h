@@ -124,10 +124,12 @@ typedef struct {
                          on the two x faces only; y and z must be periodic. */
   int storage;        /* lbm_storage */
   int fp64_moments;   /* 1: moment sums and temperature recovery to FP64 quality for FP32/FP16/
-                         BF16 storage (no effect for LBM_F64), by cascaded double-word (float +
-                         float, ~2^-48 relative) sums at FP32 rates: FP32 storage over the 81
-                         values, FP16/BF16 over each shell's offsets, weighted by the shell's
-                         weights held as double words; 0: FP32 */
+                         BF16 storage (no effect for LBM_F64), without FP64 arithmetic: FP32
+                         storage by exact 64-bit integer sums of the values scaled by a power
+                         of two, FP16/BF16 by cascaded double-word (float + float, ~2^-48
+                         relative) sums of each shell's offsets, weighted by the shell's
+                         weights held as double words; u and theta then in double-word
+                         arithmetic; 0: FP32 */
   void* cuda_stream;  /* cudaStream_t the context issues its work on; NULL: the context
                          creates its own stream (which synchronises with the legacy
                          default stream) */
