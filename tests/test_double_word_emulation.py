@@ -97,7 +97,15 @@ def _fixed_moments(f, h, pairs, rest):
     K = min(61 - e, 120)
 
     def q(v):
-        return int(np.rint(np.float64(v) * 2.0 ** K))  # f 2^K is exact in FP64 too
+        t = np.float64(v) * 2.0 ** K  # f 2^K: exact in FP32, and so in FP64
+        # the kernel's conversion: a = rint(t 2^-31), b = t - a 2^31 (an exact float), then
+        # rint(t) = a 2^31 + rint(b) from two 32-bit conversions
+        a = np.rint(t * 2.0 ** -31)
+        b = t - a * 2.0 ** 31
+        assert abs(a) <= 2.0 ** 30 and abs(b) <= 2.0 ** 30 and np.float64(f32(b)) == b
+        r = int(a) * 2 ** 31 + int(np.rint(b))
+        assert r == int(np.rint(t))
+        return r
 
     tot = {"r": q(f[rest]), "e": 0, "x": 0, "y": 0, "z": 0}
     peak = abs(tot["r"])
