@@ -2,6 +2,7 @@
 // read-back, raw population get/set (FP64, dense layout), boundary ghost layers, and the
 // deterministic global conservation sums.
 #include "device_common.cuh"
+#include "reduce.cuh"
 
 namespace lbm {
 
@@ -460,8 +461,8 @@ __global__ void aa_ghost_push_kernel(Geometry g, LatticeTables tab, S* buf, int 
 }
 
 // Global sums (rho, j_x, j_y, j_z, <f, c^2>) over all sites.  Pass 1: per-block partials
-// (fixed grid, fixed per-thread order); pass 2: one block sums them in a fixed order, so
-// the result is bitwise reproducible.
+// (fixed grid, fixed per-thread order, then warp-shuffle trees); pass 2: one warp sums them
+// (fixed lane striding, then a shuffle tree), so the result is bitwise reproducible.
 template <class S>
 __global__ void totals_pass1(Geometry g, LatticeTables tab, const S* buf, int layout, double* partials) {
   const long long n = static_cast<long long>(g.nx) * g.ny * g.nz;
@@ -477,23 +478,14 @@ __global__ void totals_pass1(Geometry g, LatticeTables tab, const S* buf, int la
     acc[3] += jz;
     acc[4] += e;
   }
-  __shared__ double sh[5][kAuxBlock];
-  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int w = kAuxBlock / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+  block_sum5_fixed<kAuxBlock>(acc);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 5; ++q) partials[blockIdx.x * 5 + q] = acc[q];
 }
 
+// one warp
 __global__ void totals_pass2(const double* partials, int nblocks, double* out) {
-  if (threadIdx.x < 5) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  warp_total5_fixed(partials, nblocks, out);
 }
 
 unsigned blocks_for(long long n) { return static_cast<unsigned>((n + kAuxBlock - 1) / kAuxBlock); }

@@ -7,6 +7,7 @@
 #include <mutex>
 
 #include "device_common.cuh"
+#include "reduce.cuh"
 #include "lbm.h"
 
 namespace lbm {
@@ -61,23 +62,14 @@ __global__ void na_pass1(const S* __restrict__ f, long long n, LatticeTables tab
     acc[3] += jz;
     acc[4] += e;
   }
-  __shared__ double sh[5][kNaThreads];
-  for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] = acc[q];
-  __syncthreads();
-  for (int w = kNaThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int q = 0; q < 5; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 5) partials[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+  block_sum5_fixed<kNaThreads>(acc);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 5; ++q) partials[blockIdx.x * 5 + q] = acc[q];
 }
 
+// one warp
 __global__ void na_pass2(const double* partials, int nblocks, double* out) {
-  if (threadIdx.x < 5) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[b * 5 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
+  warp_total5_fixed(partials, nblocks, out);
 }
 
 // Address of the static array on the current device, looked up once per device (the first
