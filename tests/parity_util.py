@@ -92,13 +92,17 @@ def site_coords(wl, sites):
     return sub, t % wl.nx, (t // wl.nx) % wl.ny, t // (wl.nx * wl.ny)
 
 
-def oracle_sampled_step(wl, sites, tau):
+def oracle_sampled_step(wl, sites, tau, eq="series", collision="bgk", store=None):
     """One step of the oracle at selected sites of a periodic grid, computed site by site
-    from the initial state f = feq(fields): each target pulls its 81 populations from the
-    equilibria of its source sites (index maps of oracle.pull_displacement), then moments,
-    equilibrium and collision.  Returns post-collision populations [81, K], oracle order."""
+    from the initial state f = feq(fields) (App. B series, or the exact entropic equilibrium
+    with eq="entropic"): each target pulls its 81 populations from the equilibria of its source
+    sites (index maps of oracle.pull_displacement), then moments, equilibrium and collision (BGK,
+    or the entropic alpha of Eq. (delH) with collision="entropic").  store(f [81, U]), if given,
+    maps the initial populations to the values a storage format holds.  Returns post-collision
+    populations [81, K], oracle order."""
     assert all((f if isinstance(f, str) else f[0]) == "periodic" for f in wl.faces)
     lat = O.velocity_set()
+    feq_of = (lambda r, u, t: O.entropic_equilibrium(r, u, t, lat)[0]) if eq == "entropic" else O.equilibrium
     n = wl.nx * wl.ny * wl.nz
     sub, x, y, z = site_coords(wl, sites)
     src = np.empty((lat.q, len(sub)), dtype=np.int64)
@@ -115,7 +119,11 @@ def oracle_sampled_step(wl, sites, tau):
     rho = wl.rho.reshape(-1)[uniq]
     u = wl.u.reshape(3, -1)[:, uniq]
     th = wl.theta.reshape(-1)[uniq]
-    feq_src = O.equilibrium(rho, u, th)                     # [81, U]
+    feq_src = feq_of(rho, u, th)                            # [81, U]
+    if store is not None:
+        feq_src = store(feq_src)
     pulled = feq_src[np.arange(lat.q)[:, None], inv]        # [81, K]
     r, uu, t = O.moments(pulled)
-    return O.collide(pulled, O.equilibrium(r, uu, t), tau)
+    feq = feq_of(r, uu, t)
+    alpha = O.entropic_alpha(pulled, feq) if collision == "entropic" else 2.0
+    return O.collide(pulled, feq, tau, alpha=alpha)

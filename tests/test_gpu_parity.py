@@ -263,15 +263,25 @@ def test_device_pointer_path_matches_host(B):
         B.lbm_destroy(ctx)
 
 
-def _sampled_full_size(B, perm, wlib, wl, storage, tol, nsamples=96):
+def _round_f16_offsets(f):
+    """The values FP16 offset storage holds for populations f [81, ...] (oracle order):
+    w (1 + d) with d = f / w - 1 rounded to FP16."""
+    w = O.velocity_set().w.reshape((81,) + (1,) * (f.ndim - 1))
+    return w * (1.0 + (f / w - 1.0).astype(np.float16).astype(np.float64))
+
+
+def _sampled_full_size(B, perm, wlib, wl, storage, tol, nsamples=96, eq="series", collision="bgk",
+                       fp64_moments=False):
     tau = wl.paper_tau("lb")
     rng = np.random.default_rng(123)
     n = wl.nx * wl.ny * wl.nz
     # random sites plus the corners and faces of both sublattices (wrap-around paths)
     edge = [0, wl.nx - 1, n - 1, n - wl.nx, n, 2 * n - 1, n + wl.nx * wl.ny - 1]
     sites = np.unique(np.concatenate([rng.integers(0, 2 * n, nsamples), edge]))
-    ref = oracle_sampled_step(wl, sites, tau)[perm].T         # [K, 81] library order
-    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage)
+    store = _round_f16_offsets if storage == "f16" else None
+    ref = oracle_sampled_step(wl, sites, tau, eq=eq, collision=collision, store=store)[perm].T  # [K, 81]
+    cfg = B.make_config(wl.nx, wl.ny, wl.nz, tau, storage, fp64_moments=fp64_moments, equilibrium=eq,
+                        collision=collision)
     ctx = B.lbm_create(cfg)
     try:
         B.lbm_init(ctx, wl.rho.reshape(-1), wl.u.reshape(-1), wl.theta.reshape(-1))
@@ -280,8 +290,14 @@ def _sampled_full_size(B, perm, wlib, wl, storage, tol, nsamples=96):
     finally:
         B.lbm_destroy(ctx)
     err = np.max(np.abs(got - ref) / (wlib * np.maximum(1.0, np.abs(ref / wlib))))
-    print("%s %s sampled 1-step population error %.3g" % (wl.name, storage, err))
+    print("%s %s %s/%s%s sampled 1-step population error %.3g" %
+          (wl.name, storage, eq, collision, " fp64 moments" if fp64_moments else "", err))
     assert err <= tol, err
+
+
+@pytest.fixture(scope="module")
+def tgv512():
+    return W.taylor_green(512)
 
 
 # FP32 per-population bound for one step from FP32 inputs: the FP32 evaluation of the
@@ -291,6 +307,30 @@ def test_full_size_tgv128_sampled(B, perm, wlib, storage, tol):
     _sampled_full_size(B, perm, wlib, W.taylor_green(128), storage, tol)
 
 
-def test_full_size_tgv512_fp32_sampled(B, perm, wlib):
+def test_full_size_tgv512_fp32_sampled(B, perm, wlib, tgv512):
     """The roofline point of the benchmark: 512^3 TGV, FP32 storage (2 x 87 GB)."""
-    _sampled_full_size(B, perm, wlib, W.taylor_green(512), "f32", 4e-5, nsamples=64)
+    _sampled_full_size(B, perm, wlib, tgv512, "f32", 4e-5, nsamples=64)
+
+
+def test_full_size_tgv512_fp32_fp64_moments_sampled(B, perm, wlib, tgv512):
+    """512^3 TGV, FP32 storage with FP64-quality moments (exact integer sums), as the bench
+    times it."""
+    _sampled_full_size(B, perm, wlib, tgv512, "f32", 4e-5, nsamples=64, fp64_moments=True)
+
+
+def test_full_size_tgv512_fp16_sampled(B, perm, wlib, tgv512):
+    """512^3 TGV, FP16 offsets: the two-sites-per-thread kernel as the bench times it.  The
+    oracle steps the FP16-rounded initial state; the kernel's FP32 arithmetic and its rounding of
+    the result to FP16 leave at most about one FP16 unit of the offset (4.9e-4 below |d| = 1);
+    measured 4.3e-4."""
+    _sampled_full_size(B, perm, wlib, tgv512, "f16", 1.3e-3, nsamples=64)
+
+
+@pytest.mark.parametrize("collision", ["bgk", "entropic"])
+def test_full_size_tgv256_entropic_sampled(B, perm, wlib, collision):
+    """256^3 TGV, FP32 storage, exact entropic equilibrium with BGK or with the entropic alpha
+    (the kernels of the served mix and the entropic-alpha bench line), sampled one step.  The FP32
+    Newton for the multipliers stops at 1e-6 of the moments; measured 1.9e-5 (BGK) and 1.8e-5
+    (entropic alpha)."""
+    _sampled_full_size(B, perm, wlib, W.taylor_green(256), "f32", 6e-5, nsamples=64, eq="entropic",
+                       collision=collision)
