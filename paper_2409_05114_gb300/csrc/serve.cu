@@ -326,7 +326,7 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
   SRV_CK(s, cudaHostGetDevicePointer(reinterpret_cast<void**>(&din), r->in.p, 0));
   SRV_CK(s, launch_init(r->cfg.storage, r->cfg.equilibrium, res.g, s->tab, res.buf[0], din, din + S, din + 4 * S, 0, S,
                         S, s->admit, s->d_flags + slot));
-  ++s->stats.kernel_launches;
+  long long launches = 1;  // published under the lock below, with the stats' readers
   for (int face = 0; face < 2; ++face) {
     const lbm_bc& b = r->cfg.face[face];
     if (b.kind != LBM_BC_EQ_INFLOW) continue;
@@ -337,12 +337,14 @@ lbm_status start_admission(lbm_server* s, const std::shared_ptr<Request>& r, int
       equilibrium_f64(b.rho, b.ux, b.uy, b.uz, b.theta, s->tab, feq.v);
     for (int k = 0; k < 2; ++k) {
       SRV_CK(s, launch_fill_inflow(r->cfg.storage, res.g, s->tab, res.buf[k], face, feq, s->admit));
-      ++s->stats.kernel_launches;
+      ++launches;
     }
   }
   SRV_CK(s, cudaEventCreateWithFlags(&res.ready, cudaEventDisableTiming));
   SRV_CK(s, cudaEventRecord(res.ready, s->admit));
   s->joining.push_back(res);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stats.kernel_launches += launches;
   return LBM_OK;
 }
 
@@ -553,11 +555,14 @@ lbm_status run_tick(lbm_server* s) {
   if (!g) return set_fatal(s, "CUDA graph capture of a serving tick failed");
   SRV_CK(s, cudaGraphLaunch(g, s->compute));
   SRV_CK(s, cudaEventRecord(s->tick_done, s->compute));
-  ++s->stats.graph_launches;
   int groups = 0;
   for (int gi = 0; gi < kGroups; ++gi) groups += plan.count[gi] > 0;
-  s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + 2 * groups);
-  ++s->stats.ticks;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    ++s->stats.graph_launches;
+    s->stats.kernel_launches += static_cast<long long>(K) * ((total_rows > 0 ? 1 : 0) + 2 * groups);
+    ++s->stats.ticks;
+  }
   SRV_CK(s, cudaMemcpyAsync(s->h_flags, s->d_flags, sizeof(unsigned int) * s->max_cases, cudaMemcpyDeviceToHost,
                             s->compute));
   // overlap: admit newly arrived requests while the tick runs
