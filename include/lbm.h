@@ -318,7 +318,7 @@ lbm_status lbm_wait(lbm_server* srv, long long ticket, double timeout_s);
 lbm_status lbm_server_get_stats(lbm_server* srv, lbm_server_stats* out);
 
 /* Message of the server's last failure (or of the last failed lbm_server_create when srv
- * is NULL). */
+ * is NULL).  The string stays valid until the calling thread's next call of this function. */
 const char* lbm_server_last_error(const lbm_server* srv);
 
 /* Stops the scheduler (queued and running cases are dropped) and frees everything. */

@@ -775,7 +775,13 @@ lbm_status lbm_server_get_stats(lbm_server* s, lbm_server_stats* out) {
 
 const char* lbm_server_last_error(const lbm_server* s) {
   if (!s) return lbm::g_server_error.c_str();
-  return s->err.c_str();
+  // a copy taken under the lock: the scheduler thread may replace the message meanwhile
+  thread_local std::string copy;
+  {
+    std::lock_guard<std::mutex> lk(const_cast<lbm_server*>(s)->mu);
+    copy = s->err;
+  }
+  return copy.c_str();
 }
 
 lbm_status lbm_server_destroy(lbm_server* s) {
