@@ -298,7 +298,8 @@ lbm_status lbm_server_create(size_t hbm_budget_bytes, int max_cases, lbm_server*
  * the series equilibrium of App. B or the exact entropic equilibrium of Sec. III, BGK collision,
  * ping-pong streaming, x faces periodic, zero-gradient or equilibrium inflow; cuda_stream is
  * ignored), initial fields in host memory (layout as lbm_init; copied into pinned host memory
- * of the request's own, 80 bytes per site with its result, before the call returns) and
+ * of the request's own, 80 bytes per site with its result, before the call returns; released
+ * when lbm_poll hands the result over, or by lbm_server_destroy) and
  * nsteps >= 1.  Returns a ticket.  LBM_ENOMEM if the case alone exceeds the budget or its
  * pinned memory cannot be allocated, LBM_EINVAL for an invalid configuration. */
 lbm_status lbm_submit(lbm_server* srv, const lbm_config* cfg, const double* rho, const double* u,
